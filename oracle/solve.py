@@ -1,0 +1,112 @@
+"""Solves of the SPD pressure-stress system (eq. stokesmixedsystemspd).
+
+The method's result is the exact solution of a linear system, so the oracle
+solves it directly where it can and by plain FP64 Jacobi-preconditioned CG
+(the textbook algorithm; the paper used CG with a domain-decomposition
+preconditioner, Section 9) where it cannot.  The relative residual is
+||b - A x||_2 / ||b||_2, recomputed from scratch.
+"""
+import time
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+
+def relative_residual(A, x, b):
+    nb = np.linalg.norm(b)
+    if nb == 0:
+        return float(np.linalg.norm(A @ x))
+    return float(np.linalg.norm(b - A @ x) / nb)
+
+
+def solve_direct(A, b, null_vectors=()):
+    """Sparse LU solve.  Each null vector (enclosed-liquid pressure mode,
+    Section 8) is removed by fixing one of its entries to zero, as the paper
+    suggests; the returned x is one solution of the consistent system."""
+    n = A.shape[0]
+    pin = [int(np.flatnonzero(v)[0]) for v in null_vectors]
+    keep = np.setdiff1d(np.arange(n), pin)
+    Ak = A.tocsc()[keep][:, keep]
+    x = np.zeros(n)
+    x[keep] = spla.spsolve(Ak, b[keep])
+    return x
+
+
+def cholesky_ok(A):
+    """Dense Cholesky of a small matrix: True if A is positive definite."""
+    try:
+        sla.cholesky(A.toarray(), lower=True)
+        return True
+    except sla.LinAlgError:
+        return False
+
+
+def pcg(A, b, tol=1e-8, max_iter=100000, x0=None, M_inv=None, true_check=True):
+    """Jacobi-preconditioned conjugate gradient in FP64.
+
+    Stops when the recurrence residual satisfies ||r|| <= tol ||b||; then the
+    true residual is recomputed and, if it is above tol, CG restarts from the
+    current x with r = b - A x.  Returns (x, iterations, true relative residual).
+    """
+    A = sp.csr_matrix(A)
+    n = b.size
+    if M_inv is None:
+        d = A.diagonal()
+        M_inv = np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0), 0.0)
+    x = np.zeros(n) if x0 is None else x0.astype(np.float64).copy()
+    nb = np.linalg.norm(b)
+    if nb == 0:
+        return np.zeros(n), 0, 0.0
+    it = 0
+    for _restart in range(20):
+        r = b - A @ x
+        if np.linalg.norm(r) <= tol * nb:
+            break
+        z = M_inv * r
+        p = z.copy()
+        rz = r @ z
+        while it < max_iter:
+            q = A @ p
+            pq = p @ q
+            if pq <= 0:
+                break
+            alpha = rz / pq
+            x += alpha * p
+            r -= alpha * q
+            it += 1
+            if np.linalg.norm(r) <= tol * nb:
+                break
+            z = M_inv * r
+            rz_new = r @ z
+            p = z + (rz_new / rz) * p
+            rz = rz_new
+        if not true_check or it >= max_iter:
+            break
+    return x, it, relative_residual(A, x, b)
+
+
+def time_pcg_iterations(A, b, iters):
+    """Wall time of ``iters`` iterations of ``pcg`` (no convergence test), for
+    the CPU baseline.  Returns seconds."""
+    A = sp.csr_matrix(A)
+    d = A.diagonal()
+    M_inv = np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0), 0.0)
+    x = np.zeros(b.size)
+    r = b.copy()
+    z = M_inv * r
+    p = z.copy()
+    rz = r @ z
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        q = A @ p
+        alpha = rz / (p @ q)
+        x += alpha * p
+        r -= alpha * q
+        np.linalg.norm(r)
+        z = M_inv * r
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return time.perf_counter() - t0

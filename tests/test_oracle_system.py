@@ -1,0 +1,229 @@
+"""Pins of the assembled SPD system (oracle.system) that do not come from it:
+operator identities on polynomial and rigid fields, the textbook interior
+stencils, symmetry, positive definiteness, equivalence with the indefinite
+KKT system, and the exactness cases of Section 9 (hydrostatic, rigid
+translation and rotation)."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import operators as O
+from oracle import solve as So
+from oracle import system as S_
+from paper_1010_2832_gb300 import workloads as W
+
+
+def _system(wl, **kw):
+    return S_.build_system(S_.StokesInput(**wl.as_oracle_kwargs()), **kw)
+
+
+def _face_field(n, h, origin, fn):
+    dim = len(n)
+    parts = []
+    for d, f in enumerate(W.FACES[dim]):
+        P = W.sample_points(f, n, h, origin)
+        parts.append(np.broadcast_to(fn(d, P), P[0].shape).ravel())
+    return np.concatenate(parts)
+
+
+def test_divergence_of_linear_field_exact():
+    n, h, o = (6, 5), 0.2, (0.0, 0.0)
+    u = _face_field(n, h, o, lambda d, P: (1.5 * P[0] - 0.7 * P[1] + 0.2) if d == 0 else (0.3 * P[0] + 2.5 * P[1]))
+    div = -(O.gradient_transpose(n, h) @ u)
+    assert np.allclose(div, 1.5 + 2.5, atol=1e-12)
+
+
+def test_deformation_rows_on_linear_field_2d():
+    n, h, o = (6, 5), 0.2, (0.0, 0.0)
+    # u = a x + b y, v = c x + d y:  tau_xx row -> a - d, tau_xy row -> b + c
+    a, b, c, d = 1.3, -0.4, 0.9, 0.25
+    u = _face_field(n, h, o, lambda k, P: (a * P[0] + b * P[1]) if k == 0 else (c * P[0] + d * P[1]))
+    D = O.deformation(n, h)
+    r = D @ u
+    ncell = n[0] * n[1]
+    assert np.allclose(r[:ncell], a - d, atol=1e-12)
+    # interior nodes only (boundary node rows drop ghost faces)
+    nodes = r[ncell:].reshape(n[1] + 1, n[0] + 1)
+    assert np.allclose(nodes[1:-1, 1:-1], b + c, atol=1e-12)
+
+
+def test_deformation_rows_on_linear_field_3d():
+    n, h, o = (4, 5, 3), 0.25, (0.0, 0.0, 0.0)
+    J = np.array([[0.7, -0.2, 0.4], [0.5, 1.1, -0.3], [0.2, 0.6, -0.9]])  # du_i/dx_j
+    u = _face_field(n, h, o, lambda k, P: J[k, 0] * P[0] + J[k, 1] * P[1] + J[k, 2] * P[2])
+    r = O.deformation(n, h) @ u
+    nx, ny, nz = n
+    nc = nx * ny * nz
+    assert np.allclose(r[:nc], J[0, 0] - J[2, 2], atol=1e-12)
+    assert np.allclose(r[nc:2 * nc], J[1, 1] - J[2, 2], atol=1e-12)
+    o2 = 2 * nc
+    exy = r[o2:o2 + nz * (ny + 1) * (nx + 1)].reshape(nz, ny + 1, nx + 1)
+    assert np.allclose(exy[:, 1:-1, 1:-1], J[0, 1] + J[1, 0], atol=1e-12)
+    o3 = o2 + exy.size
+    exz = r[o3:o3 + (nz + 1) * ny * (nx + 1)].reshape(nz + 1, ny, nx + 1)
+    assert np.allclose(exz[1:-1, :, 1:-1], J[0, 2] + J[2, 0], atol=1e-12)
+    eyz = r[o3 + exz.size:].reshape(nz + 1, ny + 1, nx)
+    assert np.allclose(eyz[1:-1, 1:-1, :], J[1, 2] + J[2, 1], atol=1e-12)
+
+
+def test_rigid_rotation_has_zero_divergence_and_strain():
+    n, h, o = (7, 6), 0.15, (-0.5, -0.4)
+    u = _face_field(n, h, o, lambda d, P: -0.8 * P[1] if d == 0 else 0.8 * P[0])
+    assert np.abs(O.gradient_transpose(n, h) @ u).max() < 1e-13
+    r = O.deformation(n, h) @ u
+    ncell = n[0] * n[1]
+    assert np.abs(r[:ncell]).max() < 1e-13
+    # boundary nodes see ghost faces (dropped), so only interior nodes vanish
+    nodes = r[ncell:].reshape(n[1] + 1, n[0] + 1)
+    assert np.abs(nodes[1:-1, 1:-1]).max() < 1e-13
+
+
+def test_interior_stencil_is_textbook():
+    """All-liquid box, no interior solid: interior rows of A are
+    A22 = (dt/rho)(-Lap_h), A11[txx] = 1/mu + (dt/rho)(-Lap_h) and
+    A12 = (dt/rho)(d_xx - d_yy), with the 5-point stencils on h."""
+    n = 8
+    rho, mu, dt = 2.0, 0.5, 0.1
+    wl = W.full_box(n, 2)
+    wl.rho = [np.full_like(r, rho) for r in wl.rho]
+    wl.mu = [np.full_like(m, mu) for m in wl.mu]
+    wl.dt = dt
+    S = _system(wl)
+    A = S.A.tocsr()
+    h = wl.h
+    nc, nn = n * n, (n + 1) ** 2
+    k = dt / (rho * h * h)
+    i, j = 4, 3
+    c = j * n + i
+    txx, p = c, nc + nn + c
+    assert A[p, p] == pytest.approx(4 * k)
+    assert A[p, p + 1] == pytest.approx(-k)
+    assert A[p, p + n] == pytest.approx(-k)
+    assert A[txx, txx] == pytest.approx(1 / mu + 4 * k)
+    assert A[txx, txx + 1] == pytest.approx(-k)
+    assert A[txx, txx + n] == pytest.approx(-k)
+    # A12 = (dt/rho) (delta_xx - delta_yy) p
+    assert A[txx, p] == pytest.approx(0.0, abs=1e-9)
+    assert A[txx, p + 1] == pytest.approx(k)
+    assert A[txx, p - 1] == pytest.approx(k)
+    assert A[txx, p + n] == pytest.approx(-k)
+    # tau_xy node (i, j): (1/mu) + (dt/rho)(-Lap_h) on nodes
+    t = nc + j * (n + 1) + i
+    assert A[t, t] == pytest.approx(1 / mu + 4 * k)
+    assert A[t, t + 1] == pytest.approx(-k)
+
+
+CASES = [(2, (8, 7)), (2, (12, 12)), (2, (10, 6)), (3, (5, 4, 6)), (3, (6, 6, 5))]
+
+
+@pytest.mark.parametrize("dim,n", CASES)
+@pytest.mark.parametrize("seed", range(4))
+def test_symmetric_positive_definite_and_kkt_equivalent(dim, n, seed):
+    S = _system(W.random_small(n, seed=seed, dim=dim))
+    A = S.A
+    assert abs(A - A.T).max() <= 1e-14 * abs(A).max()
+    nulls = S_.pressure_null_vectors(S)
+    if not nulls:
+        assert So.cholesky_ok(A)
+    x = So.solve_direct(A, S.b, nulls)
+    Kmat, r, lv, ac = S_.kkt_system(S)
+    z = spla.spsolve(Kmat.tocsc(), r)
+    u = S_.recover_velocity(S, x)
+    scale_u = max(np.abs(z[:lv.size]).max(), 1e-30)
+    assert np.abs(u[lv] - z[:lv.size]).max() <= 1e-7 * scale_u
+    if not nulls:
+        scale_x = max(np.abs(z[lv.size:]).max(), 1e-30)
+        assert np.abs(x[ac] - z[lv.size:]).max() <= 1e-6 * scale_x
+
+
+def test_solid_side_rule_removes_a_null_space():
+    """Without the solid-side invalidation (a face next to a zero-fluid-weight
+    multiplier) the pressure and stress of a fully solid cell that touches one
+    live face form a null vector; with it the matrix is definite."""
+    wl = W.bumps_2d(24, seed=7, rho_split=False)
+    S1 = _system(wl, solid_side_rule=False)
+    S2 = _system(wl)
+    assert not So.cholesky_ok(S1.A)
+    assert So.cholesky_ok(S2.A)
+
+
+def _exactness_system(wl):
+    S = _system(wl)
+    x = So.solve_direct(S.A, S.b, S_.pressure_null_vectors(S))
+    return S, x, S_.recover_velocity(S, x)
+
+
+def test_rigid_translation_free_blob_is_exact():
+    U = (0.37, -0.81)
+    wl = W.from_functions("blob", 2, (20, 20), 1 / 20, 0.05, (0, 0),
+                          lambda X: np.hypot(X[0] - .48, X[1] - .53) - 0.27 * (1 + 0.2 * np.sin(5 * X[0])),
+                          lambda X: W.box_phi(X, (0, 0), (1, 1)),
+                          lambda P: 1.0 + P[0], lambda P: 0.2 + P[1], lambda d, P: 0.0, lambda d, P: U[d])
+    S, x, u = _exactness_system(wl)
+    assert np.abs(x).max() < 1e-10
+    assert np.abs(u[S.live] - S.u_star[S.live]).max() < 1e-12
+
+
+def test_rigid_rotation_free_blob_is_exact():
+    w = 1.7
+    rot = lambda d, P: -w * (P[1] - 0.5) if d == 0 else w * (P[0] - 0.5)
+    wl = W.from_functions("blob", 2, (22, 22), 1 / 22, 0.1, (0, 0),
+                          lambda X: np.hypot(X[0] - .5, X[1] - .5) - 0.3 - 0.04 * np.cos(3 * np.arctan2(X[1] - .5, X[0] - .5)),
+                          lambda X: W.box_phi(X, (0, 0), (1, 1)),
+                          lambda P: 1.0, lambda P: 0.3 + P[0] * P[1], lambda d, P: 0.0, rot)
+    S, x, u = _exactness_system(wl)
+    assert np.abs(x).max() < 1e-9
+    assert np.abs(u[S.live] - S.u_star[S.live]).max() < 1e-11
+
+
+def test_rigid_rotation_3d_is_exact():
+    w = np.array([0.3, -0.5, 0.8])
+    c = np.array([0.5, 0.5, 0.5])
+    def rot(d, P):
+        r = [P[k] - c[k] for k in range(3)]
+        cross = [w[1] * r[2] - w[2] * r[1], w[2] * r[0] - w[0] * r[2], w[0] * r[1] - w[1] * r[0]]
+        return cross[d]
+    wl = W.from_functions("ball", 3, (9, 9, 9), 1 / 9, 0.1, (0, 0, 0),
+                          lambda X: np.sqrt((X[0] - .5) ** 2 + (X[1] - .5) ** 2 + (X[2] - .5) ** 2) - 0.33,
+                          lambda X: W.box_phi(X, (0,) * 3, (1,) * 3),
+                          lambda P: 1.0, lambda P: 0.5, lambda d, P: 0.0, rot)
+    S, x, u = _exactness_system(wl)
+    assert np.abs(x).max() < 1e-9
+    assert np.abs(u[S.live] - S.u_star[S.live]).max() < 1e-11
+
+
+@pytest.mark.parametrize("solid", [False, True])
+def test_hydrostatic_is_exact(solid):
+    """Liquid at rest under gravity in a box (optionally around a solid disk)
+    with a flat free surface: u* = (0, -g dt) gives u = 0."""
+    g, dt = 9.81, 0.02
+    surf = 0.613
+    phiS = (lambda X: np.minimum(W.box_phi(X, (0, 0), (1, 1)), np.hypot(X[0] - .4, X[1] - .25) - .12)) if solid \
+        else (lambda X: W.box_phi(X, (0, 0), (1, 1)))
+    wl = W.from_functions("hydro", 2, (24, 24), 1 / 24, dt, (0, 0),
+                          lambda X: X[1] - surf, phiS, lambda P: 1.3, lambda P: 0.7,
+                          lambda d, P: 0.0, lambda d, P: 0.0 if d == 0 else -g * dt)
+    S, x, u = _exactness_system(wl)
+    assert np.abs(u[S.live]).max() < 1e-10
+    nc = S.sizes["cell"]
+    assert np.abs(x[:-nc]).max() < 1e-9          # all stresses vanish
+
+
+def test_moving_solid_translation_is_exact():
+    U = (0.5, -0.2)
+    disk = lambda X: np.hypot(X[0] - .5, X[1] - .45) - .15
+    wl = W.from_functions("trans", 2, (24, 24), 1 / 24, 0.05, (0, 0),
+                          lambda X: np.hypot(X[0] - .5, X[1] - .5) - 0.4,
+                          lambda X: np.minimum(W.box_phi(X, (0, 0), (1, 1)), disk(X)),
+                          lambda P: 1.0, lambda P: 0.4, lambda d, P: U[d], lambda d, P: U[d])
+    S, x, u = _exactness_system(wl)
+    assert np.abs(x).max() < 1e-9
+    assert np.abs(u[S.live] - U[0] * 0 - S.u_star[S.live]).max() < 1e-11
+
+
+def test_pcg_matches_direct():
+    S = _system(W.disk_in_box(16))
+    xd = So.solve_direct(S.A, S.b)
+    x, it, rr = So.pcg(S.A, S.b, tol=1e-13)
+    assert rr <= 1e-13
+    assert np.abs(x - xd).max() <= 1e-9 * np.abs(xd).max()
