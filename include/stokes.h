@@ -1,0 +1,227 @@
+/*
+ * libstokes: GPU solve of the pressure-stress system of one backward-Euler
+ * Stokes step on a staggered grid with embedded free surfaces and solids.
+ *
+ * The method is the variational finite-difference discretization of
+ * "A Simple Finite Difference Method for Time-Dependent, Variable
+ * Coefficient Stokes Flow on Irregular Domains": velocity is eliminated from
+ * the indefinite system eq. (stokesmixedsystem) to give the sparse
+ * symmetric positive-definite system eq. (stokesmixedsystemspd) in the
+ * deviatoric stress tau and the pressure p,
+ *
+ *     A x = b,  A = C + B K B^T,  B = [W_L^tau D ; W_L^p G^T],
+ *     K = dt P^-1 (W_L^u)^-1 W_F^u,
+ *
+ * which this library builds from level sets and coefficient fields, applies
+ * matrix-free, and solves with preconditioned conjugate gradients.  Units
+ * are SI (Appendix A).  All entry points are plain C; all array arguments
+ * are caller-owned memory of the kind stated (device = CUDA device memory on
+ * the context's device, host = ordinary host memory).
+ *
+ * Threading and streams: a context is bound to one device and one CUDA
+ * stream.  Calls on one context must not overlap from several host threads.
+ * Work is enqueued on the context's stream; calls return after enqueueing
+ * unless stated otherwise.
+ *
+ * Errors: every call returns a stokes_status; on failure the context (or,
+ * for stokes_create, a thread-local slot) keeps a message readable with
+ * stokes_last_error().  Arguments are validated on the host before any work
+ * is enqueued; an argument error leaves the context unchanged.
+ */
+#ifndef STOKES_H
+#define STOKES_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    STOKES_OK = 0,
+    STOKES_ERR_ARG = -1,            /* invalid argument (null, size, range)   */
+    STOKES_ERR_CUDA = -2,           /* a CUDA runtime call failed             */
+    STOKES_ERR_NOT_CONVERGED = -3,  /* iteration cap reached above tolerance  */
+    STOKES_ERR_BREAKDOWN = -4,      /* p.Ap <= 0 or r.z <= 0 in CG            */
+    STOKES_ERR_TIMEOUT = -5,        /* a bounded device-side wait gave up     */
+    STOKES_ERR_BOUNDS = -6,         /* device-side index check failed         */
+    STOKES_ERR_NONFINITE = -7,      /* NaN/Inf found in an input or residual  */
+    STOKES_ERR_STATE = -8           /* call out of order (e.g. no weights)    */
+} stokes_status;
+
+/* Precision of a stencil apply or of the inner solve. */
+enum {
+    STOKES_FP64 = 0,   /* FP64 vectors and coefficients                         */
+    STOKES_FP32 = 1,   /* FP32 vectors and coefficients, FP32 arithmetic        */
+    STOKES_BF16 = 2    /* FP32 vectors, BF16-stored coefficients, FP32 arithmetic */
+};
+
+/* Uniform grid of nx x ny (x nz) cells of side h, lower corner at origin.
+ * dim = 2 ignores nz and origin[2].  The grid boundary is a static wall. */
+typedef struct {
+    int dim;
+    int nx, ny, nz;
+    double h;
+    double dt;
+    double origin[3];
+} stokes_grid;
+
+typedef struct stokes_ctx_s* stokes_ctx;
+
+/*
+ * Field layouts (caller side, "field layout"): C order, x fastest.
+ *   2D: u (ny, nx+1)   v (ny+1, nx)   cells (ny, nx)   nodes (ny+1, nx+1)
+ *   3D: u (nz, ny, nx+1)  v (nz, ny+1, nx)  w (nz+1, ny, nx)
+ *       cells (nz, ny, nx)  tau_xy on z-edges (nz, ny+1, nx+1)
+ *       tau_xz on y-edges (nz+1, ny, nx+1)  tau_yz on x-edges (nz+1, ny+1, nx)
+ * Level sets live on the half lattice of spacing h/2, padded by h/2:
+ *   2D (2ny+3, 2nx+3), 3D (2nz+3, 2ny+3, 2nx+3); point (a, b, c) sits at
+ *   origin + ((a-1) h/2, (b-1) h/2, (c-1) h/2).
+ * phi_liquid < 0 in the liquid (extended into solids); phi_solid < 0 in solids.
+ */
+
+/* Create a context for one grid on the current CUDA device.  ``stream`` is a
+ * cudaStream_t; NULL makes the context create its own blocking stream, which
+ * is ordered with the legacy default stream both ways (the legacy stream
+ * itself cannot be captured into the solver's CUDA graphs).  Allocates all device work
+ * space for the grid.  Returns STOKES_ERR_ARG for dim not in {2,3},
+ * non-positive sizes, h <= 0 or dt <= 0. */
+stokes_status stokes_create(stokes_ctx* out, const stokes_grid* grid, void* stream);
+
+/* Free every resource of the context.  NULL is accepted. */
+stokes_status stokes_destroy(stokes_ctx ctx);
+
+/* Message of the last failure on this context (ctx may be NULL for the
+ * calling thread's last stokes_create failure).  Never NULL. */
+const char* stokes_last_error(stokes_ctx ctx);
+
+/*
+ * Weights, coefficients and validity masks (Section 5, volume fractions;
+ * Section 8, null-space elimination) from device arrays in field layout:
+ *   phi_liquid, phi_solid : half-lattice level sets (FP64, device)
+ *   rho[d]                : density at faces of kind d = u, v(, w)  (device)
+ *   mu[s]                 : viscosity at stress sites, 2D {cells, nodes},
+ *                           3D {cells, z-edges, y-edges, x-edges}   (device)
+ *   u_bc[d]               : prescribed solid velocity per face kind (device)
+ * Every fraction, coefficient and mask is computed on the device.  rho and
+ * mu must be positive where used.  The arrays are read during this call's
+ * kernels only; u_bc is copied.  Enqueued on the context's stream.
+ */
+stokes_status stokes_build_weights(stokes_ctx ctx, const double* phi_liquid, const double* phi_solid,
+                                   const double* const* rho, const double* const* mu,
+                                   const double* const* u_bc);
+
+/*
+ * Unknown vectors use the context's internal "slot layout": every unknown
+ * kind is stored on a padded copy of the (nx+1)(ny+1)(nz+1) vertex lattice,
+ * one field after another (2D: tau_xx, tau_xy, p; 3D: tau_xx, tau_yy,
+ * tau_xy, tau_xz, tau_yz, p).  stokes_vector_layout() returns, for element
+ * size 1, the number of elements of one field (``field_stride``, guard
+ * included), the pitch P, rows R, planes Q and the offset of the first
+ * stored element ``base``; the sample (i, j[, k]) of field f sits at
+ *     f * field_stride + base + ((k + 1) * R + (j + 1)) * P + (i + 1)   (3D)
+ *     f * field_stride + base + (j + 1) * P + (i + 1)                   (2D)
+ * and every other element is padding that must be zero on input.
+ * ``total`` = nfields * field_stride elements per vector.
+ */
+typedef struct {
+    int nfields;
+    int64_t field_stride;
+    int64_t base;
+    int pitch, rows, planes;
+    int64_t total;
+} stokes_layout;
+
+stokes_status stokes_vector_layout(stokes_ctx ctx, stokes_layout* out);
+
+/*
+ * y = A x, matrix-free (eq. stokesmixedsystemspd in the factored form of
+ * Section 7: face values z = K B^T x, then y = B z + C x).  x, y are device
+ * vectors in slot layout of element type double (STOKES_FP64) or float
+ * (STOKES_FP32, STOKES_BF16).  Inactive unknowns act as the identity.
+ * Requires stokes_build_weights.  x and y must not alias.
+ */
+stokes_status stokes_apply(stokes_ctx ctx, const void* x, void* y, int precision);
+
+/* Right-hand side b (FP64 slot layout, device) of eq. stokesmixedsystemspd
+ * with the prescribed-velocity terms of Section 6.2, for input velocity
+ * u_star[d] (device, field layout). */
+stokes_status stokes_rhs(stokes_ctx ctx, const double* const* u_star, double* b);
+
+/* Velocity recovery (first block row of eq. stokesmixedsystem) from a
+ * solution x (FP64 slot layout, device) into u_out[d] (device, field
+ * layout): live faces u* - dt/(rho W_L) (B^T x); faces with zero effective
+ * fluid weight u_BC; fluid faces without liquid u*. */
+stokes_status stokes_recover(stokes_ctx ctx, const double* const* u_star, const double* x,
+                             double* const* u_out);
+
+typedef struct {
+    int mode;          /* STOKES_FP64: FP64 PCG; STOKES_FP32 / STOKES_BF16:
+                          inner PCG in that precision inside FP64 iterative
+                          refinement                                         */
+    double tol;        /* target true relative residual ||b-Ax||/||b||       */
+    int max_iter;      /* cap on total (inner) CG iterations                */
+    double inner_tol;  /* relative tolerance of each inner solve (mixed)    */
+    int max_outer;     /* cap on refinement steps (mixed)                    */
+    int check_every;   /* iterations between host convergence checks        */
+    int precond;       /* 0 = Jacobi (point diagonal)                        */
+} stokes_options;
+
+typedef struct {
+    int status;              /* stokes_status of the solve                  */
+    int iterations;          /* total CG iterations (inner ones if mixed)   */
+    int outer;               /* refinement steps (mixed), 1 for FP64 PCG    */
+    double rel_residual;     /* final true relative residual in FP64        */
+    double ms_rhs, ms_solve, ms_recover;  /* device time per phase          */
+} stokes_stats;
+
+/* Fill ``o`` with defaults: FP64 mode, tol 1e-8, max_iter 200000,
+ * inner_tol 1e-4, max_outer 40, check_every 64, Jacobi. */
+void stokes_default_options(stokes_options* o);
+
+/*
+ * One implicit step (the hot path): b from u*, solve A x = b to the
+ * requested true relative residual, recover u.  Inputs u_star[d] and outputs
+ * u_out[d], tau_out[s] (stress kinds in slot-field order without p) and
+ * p_out are device arrays in field layout; inactive unknowns come out 0.
+ * Synchronises the context's stream once at the end to fill ``stats``
+ * (may be NULL).  Returns STOKES_ERR_NOT_CONVERGED with the best x found if
+ * the caps are reached first.
+ */
+stokes_status stokes_solve_step(stokes_ctx ctx, const double* const* u_star, double* const* u_out,
+                                double* const* tau_out, double* p_out, const stokes_options* opt,
+                                stokes_stats* stats);
+
+/* Solve A x = b for a given right-hand side (FP64 slot layout, device);
+ * x (same layout) is overwritten.  Same options and statistics. */
+stokes_status stokes_solve_system(stokes_ctx ctx, const double* b, double* x, const stokes_options* opt,
+                                  stokes_stats* stats);
+
+/*
+ * Export of the weights for checking: ``what`` selects
+ *   0: W_L per sample kind, 1: W_F per sample kind (FP64, kinds in the order
+ *      2D {cell, node, u, v}, 3D {cell, u, v, w, exy, exz, eyz}, each in field
+ *      layout, concatenated);
+ *   2: face flags (one byte per face, field layout, u then v (then w)):
+ *      bit0 live, bit1 bad, bit2 invalid (solid side), bit3 on the wall;
+ *   3: unknown activity (one byte per unknown, stress kinds then p, field
+ *      layout).
+ * ``out`` is a device buffer of at least stokes_export_size() bytes.
+ */
+stokes_status stokes_export(stokes_ctx ctx, int what, void* out);
+int64_t stokes_export_size(stokes_ctx ctx, int what);
+
+/* Copy an unknown vector between slot layout (FP64) and field layout
+ * (concatenation of the stress fields then p, FP64).  Device pointers. */
+stokes_status stokes_slots_to_fields(stokes_ctx ctx, const double* slots, double* fields);
+stokes_status stokes_fields_to_slots(stokes_ctx ctx, const double* fields, double* slots);
+
+/* Device time (ms) of the last stokes_apply call, measured with CUDA events
+ * on the context's stream (synchronises).  Returns -1 if none. */
+double stokes_last_apply_ms(stokes_ctx ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STOKES_H */

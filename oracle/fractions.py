@@ -63,11 +63,11 @@ def tetrahedron_fraction(v):
     k = (s < 0).sum(axis=-1)
     out = np.zeros(s0.shape)
     with np.errstate(divide="ignore", invalid="ignore"):
-        f1 = s0 ** 3 / ((s0 - s1) * (s0 - s2) * (s0 - s3))
+        f1 = s0 * s0 * s0 / ((s0 - s1) * (s0 - s2) * (s0 - s3))
         x, y, p, q = s0, s1, s2, s3
         num = x * x * y * y - (p + q) * x * y * (x + y) + p * q * (x * x + x * y + y * y)
         f2 = num / ((x - p) * (x - q) * (y - p) * (y - q))
-        f3 = 1.0 - s3 ** 3 / ((s3 - s0) * (s3 - s1) * (s3 - s2))
+        f3 = 1.0 - s3 * s3 * s3 / ((s3 - s0) * (s3 - s1) * (s3 - s2))
     out = np.where(k == 1, f1, out)
     out = np.where(k == 2, f2, out)
     out = np.where(k == 3, f3, out)
@@ -87,7 +87,17 @@ def cv_fraction_2d(phi, a, b):
     total = 0.0
     for t in range(8):
         total = total + triangle_fraction(np.stack([c, ring[t], ring[(t + 1) % 8]], axis=-1))
-    return total / 8.0
+    return _by_signs(np.stack([c] + ring, axis=-1), total / 8.0)
+
+
+def _by_signs(vals, frac):
+    """Uniform-sign CVs are exactly 0 (no value < 0) or 1 (no value > 0).
+    (The simplex formulas give the same, so this only skips work.)  Mixed CVs
+    keep the computed value, which may underflow to 0 for a vanishing sliver;
+    every later W > 0 test is on this value."""
+    neg = (vals < 0).any(axis=-1)
+    pos = (vals > 0).any(axis=-1)
+    return np.where(~neg, 0.0, np.where(~pos, 1.0, frac))
 
 
 def cv_fraction_3d(phi, a, b, c):
@@ -115,7 +125,8 @@ def cv_fraction_3d(phi, a, b, c):
             for t in range(4):
                 total = total + tetrahedron_fraction(
                     np.stack([centre, fc, corners[t], corners[(t + 1) % 4]], axis=-1))
-    return total / 24.0
+    allv = np.stack([P(da, db, dc) for dc in (-1, 0, 1) for db in (-1, 0, 1) for da in (-1, 0, 1)], axis=-1)
+    return _by_signs(allv, total / 24.0)
 
 
 def cv_fraction(phi, idx):

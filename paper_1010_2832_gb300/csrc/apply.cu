@@ -1,0 +1,373 @@
+// Matrix-free apply of the SPD pressure-stress operator, eq. stokesmixedsystemspd,
+// in the factored form of Section 7: y = C x + B (K (B^T x)).
+//
+// One CTA per tile of the padded slot lattice (2D 32x8 slots, 3D 32x4x4).
+// Phase 1 stages, for the tile plus a one-slot halo, the row-weighted
+// unknowns that each face sees (for a u face: a_c (p - tau_xx) of the cells
+// on both sides and a_n tau_xy of the nodes above and below, ...).
+// Phase 2 forms the face values z_f = K_f (B^T x)_f for every face the tile
+// needs.  Phase 3 gathers y = C x + B z for the tile's own slots.
+//
+// Modes:  PLAIN  y = A x
+//         RESID  y = b - A x, block partial of ||y||^2
+//         CG     x := z + beta p_old (written to p_new for the tile), y = A x,
+//                block partial of x . y  (the CG search-direction update fused
+//                with the operator and the p.Ap dot)
+// Block partials are summed by the last block to finish (fixed order, so
+// the result is deterministic) which then updates the CG scalars.
+#include "internal.cuh"
+#include "ctx.cuh"
+
+namespace stk {
+
+template <class T> struct Acc;
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ double warp() { return warp_sum(s); }
+};
+// FP32 vectors: products and sums kept as float-float pairs (TwoProd via FMA,
+// TwoSum) so the partial is accurate to ~2^-44 relative without FP64 math.
+template <> struct Acc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ void add(float a, float b) {
+        float p = a * b;
+        float e = fmaf(a, b, -p);
+        float s, t;
+        two_sum(hi, p, s, t);
+        lo += t + e;
+        hi = s;
+    }
+    __device__ double warp() { return warp_sum_ff(hi, lo); }
+};
+
+template <class C> __device__ __forceinline__ float cvt(C v);
+template <> __device__ __forceinline__ float cvt<float>(float v) { return v; }
+template <> __device__ __forceinline__ float cvt<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double cvtd(double v) { return v; }
+
+template <class T, class C> __device__ __forceinline__ T ld(const C* p, int64_t o);
+template <> __device__ __forceinline__ double ld<double, double>(const double* p, int64_t o) { return __ldg(p + o); }
+template <> __device__ __forceinline__ float ld<float, float>(const float* p, int64_t o) { return __ldg(p + o); }
+template <> __device__ __forceinline__ float ld<float, __nv_bfloat16>(const __nv_bfloat16* p, int64_t o) {
+    return __bfloat162float(p[o]);
+}
+
+// Block reduction of one double per thread into partial[blockIdx.x], then the
+// last block sums all partials (index order) and calls fin(total).
+template <int NT, class Fin>
+__device__ void block_partial_and_finish(double v, double* partial, unsigned* counter, int nblocks, Fin fin) {
+    __shared__ double red[NT / 32];
+    __shared__ bool last;
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < NT / 32; ++q) s += red[q];
+        partial[blockIdx.x] = s;
+        __threadfence();
+        unsigned prev = atomicAdd(counter, 1u);
+        last = (prev == (unsigned)nblocks - 1u);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += NT) s += ((volatile double*)partial)[b];
+    s = warp_sum(s);
+    if (lane == 0) red[w] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int q = 0; q < NT / 32; ++q) tot += red[q];
+        fin(tot);
+        *counter = 0u;
+    }
+}
+
+template <class T, int MODE>
+__device__ __forceinline__ T stage_val(const T* x, const T* pold, T beta, int64_t o) {
+    if (MODE == MODE_CG) return x[o] + beta * pold[o];
+    return x[o];
+}
+
+// ------------------------------- 2D -----------------------------------------
+template <class T, class C, int MODE>
+__global__ void __launch_bounds__(256) k_apply2d(Layout L, const int* __restrict__ tiles, Coef<C> cf,
+                                                 const T* __restrict__ x, T* __restrict__ y, ApplyArgs args,
+                                                 int nblocks) {
+    constexpr int TY = TY2;
+    __shared__ T sU[TY + 2][TX + 2], sV[TY + 2][TX + 2], sN[TY + 2][TX + 2];
+    __shared__ T sZu[TY + 1][TX + 1], sZv[TY + 1][TX + 1];
+    if (MODE == MODE_CG && args.sc->done) return;
+    const int tile = tiles ? tiles[blockIdx.x] : blockIdx.x;
+    const int c0 = (tile % L.ntx) * TX, r0 = (tile / L.ntx) * TY;
+    const int64_t S = L.stride;
+    const C *a_c = cf.f[0], *a_n = cf.f[1], *d_c = cf.f[2], *d_n = cf.f[3], *K_u = cf.f[4], *K_v = cf.f[5];
+    const T* pold = (const T*)args.pold;
+    T* pnew = (T*)args.pnew;
+    T beta = MODE == MODE_CG ? (T)args.sc->beta : T(0);
+    const int t = threadIdx.x;
+    for (int e = t; e < (TY + 2) * (TX + 2); e += 256) {
+        int jj = e / (TX + 2), ii = e - jj * (TX + 2);
+        int64_t o = L.off(c0 - 1 + ii, r0 - 1 + jj, 0);
+        T ac = ld<T, C>(a_c, o), an = ld<T, C>(a_n, o);
+        T txx = stage_val<T, MODE>(x, pold, beta, o);
+        T txy = stage_val<T, MODE>(x + S, pold + S, beta, o);
+        T p = stage_val<T, MODE>(x + 2 * S, pold + 2 * S, beta, o);
+        if (MODE == MODE_CG && ii >= 1 && ii <= TX && jj >= 1 && jj <= TY) {
+            pnew[o] = txx; pnew[S + o] = txy; pnew[2 * S + o] = p;
+        }
+        sU[jj][ii] = ac * (p - txx);
+        sV[jj][ii] = ac * (p + txx);
+        sN[jj][ii] = an * txy;
+    }
+    __syncthreads();
+    for (int e = t; e < (TY + 1) * (TX + 1); e += 256) {
+        int jj = e / (TX + 1), ii = e - jj * (TX + 1);
+        T ku = ld<T, C>(K_u, L.off(c0 + ii, r0 - 1 + jj, 0));
+        T kv = ld<T, C>(K_v, L.off(c0 - 1 + ii, r0 + jj, 0));
+        sZu[jj][ii] = ku * ((sU[jj][ii + 1] - sU[jj][ii]) + (sN[jj][ii + 1] - sN[jj + 1][ii + 1]));
+        sZv[jj][ii] = kv * ((sV[jj + 1][ii] - sV[jj][ii]) + (sN[jj + 1][ii] - sN[jj + 1][ii + 1]));
+    }
+    __syncthreads();
+    const int tx = t & (TX - 1), ty = t / TX;
+    const int64_t o = L.off(c0 + tx, r0 + ty, 0);
+    T ac = ld<T, C>(a_c, o), an = ld<T, C>(a_n, o), dc = ld<T, C>(d_c, o), dn = ld<T, C>(d_n, o);
+    // own unknowns: the staged halo centre already holds them
+    T p_, txx, txy;
+    if (MODE == MODE_CG) {
+        txx = pnew[o]; txy = pnew[S + o]; p_ = pnew[2 * S + o];
+    } else {
+        txx = x[o]; txy = x[S + o]; p_ = x[2 * S + o];
+    }
+    T zu = sZu[ty + 1][tx], zur = sZu[ty + 1][tx + 1], zud = sZu[ty][tx];
+    T zv = sZv[ty][tx + 1], zvu = sZv[ty + 1][tx + 1], zvl = sZv[ty][tx];
+    T yp, yxx;
+    if (ac != T(0)) {
+        yp = ac * ((zu - zur) + (zv - zvu));
+        yxx = dc * txx + ac * ((zur - zu) + (zv - zvu));
+    } else {
+        yp = p_;
+        yxx = txx;
+    }
+    T yxy = dn * txy + an * ((zu - zud) + (zv - zvl));
+    if (MODE == MODE_RESID) {
+        const T* b = (const T*)args.b;
+        yxx = b[o] - yxx; yxy = b[S + o] - yxy; yp = b[2 * S + o] - yp;
+    }
+    y[o] = yxx; y[S + o] = yxy; y[2 * S + o] = yp;
+    if (MODE != MODE_PLAIN) {
+        Acc<T> acc;
+        if (MODE == MODE_RESID) { acc.add(yxx, yxx); acc.add(yxy, yxy); acc.add(yp, yp); }
+        else { acc.add(txx, yxx); acc.add(txy, yxy); acc.add(p_, yp); }
+        double v = acc.warp();
+        if ((t & 31) != 0) v = 0.0;
+        CgScalars* sc = args.sc;
+        block_partial_and_finish<256>(v, args.partial, args.counter, nblocks, [&](double tot) {
+            if (MODE == MODE_RESID) { sc->rr = tot; return; }
+            sc->pq = tot;
+            if (!(tot > 0.0) || !isfinite(tot)) { sc->done = 1; sc->status = (isfinite(tot) ? STOKES_ERR_BREAKDOWN : STOKES_ERR_NONFINITE); }
+            else sc->alpha = sc->rz / tot;
+        });
+    }
+}
+
+// ------------------------------- 3D -----------------------------------------
+// Staged helpers per slot (tile + halo):
+//   Uc = a_c (p - txx), Vc = a_c (p - tyy), Wc = a_c (p + txx + tyy)
+//   Nxy = a_xy txy, Nxz = a_xz txz, Nyz = a_yz tyz
+// Face values:
+//   z_u = K_u [Uc(c) - Uc(c-1) + Nxy(r) - Nxy(r+1) + Nxz(q) - Nxz(q+1)]
+//   z_v = K_v [Vc(r) - Vc(r-1) + Nxy(c) - Nxy(c+1) + Nyz(q) - Nyz(q+1)]
+//   z_w = K_w [Wc(q) - Wc(q-1) + Nxz(c) - Nxz(c+1) + Nyz(r) - Nyz(r+1)]
+// Gather:
+//   y_p   = a_c [z_u(c) - z_u(c+1) + z_v(r) - z_v(r+1) + z_w(q) - z_w(q+1)]
+//   y_txx = d_c (txx + tyy/2) + a_c [z_u(c+1) - z_u(c) + z_w(q) - z_w(q+1)]
+//   y_tyy = d_c (tyy + txx/2) + a_c [z_v(r+1) - z_v(r) + z_w(q) - z_w(q+1)]
+//   y_txy = d_xy txy + a_xy [z_u(r) - z_u(r-1) + z_v(c) - z_v(c-1)]
+//   y_txz = d_xz txz + a_xz [z_u(q) - z_u(q-1) + z_w(c) - z_w(c-1)]
+//   y_tyz = d_yz tyz + a_yz [z_v(q) - z_v(q-1) + z_w(r) - z_w(r-1)]
+template <class T> struct Smem3 {
+    static constexpr int SX = TX + 2, SY = TY3 + 2, SZ = TZ3 + 2, NS = SX * SY * SZ;
+    static constexpr int ZX = TX + 1, ZY = TY3 + 1, ZZ = TZ3 + 1, NZ = ZX * ZY * ZZ;
+    T U[NS], V[NS], W[NS], Nxy[NS], Nxz[NS], Nyz[NS];
+    T zu[NZ], zv[NZ], zw[NZ];
+};
+
+template <class T, class C, int MODE>
+__global__ void __launch_bounds__(256) k_apply3d(Layout L, const int* __restrict__ tiles, Coef<C> cf,
+                                                 const T* __restrict__ x, T* __restrict__ y, ApplyArgs args,
+                                                 int nblocks) {
+    using SM = Smem3<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SM& sm = *reinterpret_cast<SM*>(smem_raw);
+    if (MODE == MODE_CG && args.sc->done) return;
+    const int tile = tiles ? tiles[blockIdx.x] : blockIdx.x;
+    const int tcx = tile % L.ntx, trest = tile / L.ntx;
+    const int c0 = tcx * TX, r0 = (trest % L.nty) * TY3, q0 = (trest / L.nty) * TZ3;
+    const int64_t S = L.stride;
+    const C *a_c = cf.f[0], *a_xy = cf.f[1], *a_xz = cf.f[2], *a_yz = cf.f[3];
+    const C *d_c = cf.f[4], *d_xy = cf.f[5], *d_xz = cf.f[6], *d_yz = cf.f[7];
+    const C *K_u = cf.f[8], *K_v = cf.f[9], *K_w = cf.f[10];
+    const T* pold = (const T*)args.pold;
+    T* pnew = (T*)args.pnew;
+    T beta = MODE == MODE_CG ? (T)args.sc->beta : T(0);
+    const int t = threadIdx.x;
+    // unknown fields: 0 txx, 1 tyy, 2 txy, 3 txz, 4 tyz, 5 p
+    for (int e = t; e < SM::NS; e += 256) {
+        int ii = e % SM::SX, rest = e / SM::SX, jj = rest % SM::SY, kk = rest / SM::SY;
+        int64_t o = L.off(c0 - 1 + ii, r0 - 1 + jj, q0 - 1 + kk);
+        T v[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) v[f] = stage_val<T, MODE>(x + f * S, pold + f * S, beta, o);
+        if (MODE == MODE_CG && ii >= 1 && ii <= TX && jj >= 1 && jj <= TY3 && kk >= 1 && kk <= TZ3) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) pnew[f * S + o] = v[f];
+        }
+        T ac = ld<T, C>(a_c, o);
+        sm.U[e] = ac * (v[5] - v[0]);
+        sm.V[e] = ac * (v[5] - v[1]);
+        sm.W[e] = ac * (v[5] + v[0] + v[1]);
+        sm.Nxy[e] = ld<T, C>(a_xy, o) * v[2];
+        sm.Nxz[e] = ld<T, C>(a_xz, o) * v[3];
+        sm.Nyz[e] = ld<T, C>(a_yz, o) * v[4];
+    }
+    __syncthreads();
+    // staged index of (c, r, q) relative to (c0-1, r0-1, q0-1)
+    auto si = [](int ii, int jj, int kk) { return (kk * SM::SY + jj) * SM::SX + ii; };
+    for (int e = t; e < SM::NZ; e += 256) {
+        int ii = e % SM::ZX, rest = e / SM::ZX, jj = rest % SM::ZY, kk = rest / SM::ZY;
+        // z_u at (c0+ii, r0-1+jj, q0-1+kk): staged coords (ii+1, jj, kk)
+        {
+            int s = si(ii + 1, jj, kk);
+            T ku = ld<T, C>(K_u, L.off(c0 + ii, r0 - 1 + jj, q0 - 1 + kk));
+            sm.zu[e] = ku * ((sm.U[s] - sm.U[s - 1]) + (sm.Nxy[s] - sm.Nxy[s + SM::SX]) +
+                             (sm.Nxz[s] - sm.Nxz[s + SM::SX * SM::SY]));
+        }
+        // z_v at (c0-1+ii, r0+jj, q0-1+kk): staged (ii, jj+1, kk)
+        {
+            int s = si(ii, jj + 1, kk);
+            T kv = ld<T, C>(K_v, L.off(c0 - 1 + ii, r0 + jj, q0 - 1 + kk));
+            sm.zv[e] = kv * ((sm.V[s] - sm.V[s - SM::SX]) + (sm.Nxy[s] - sm.Nxy[s + 1]) +
+                             (sm.Nyz[s] - sm.Nyz[s + SM::SX * SM::SY]));
+        }
+        // z_w at (c0-1+ii, r0-1+jj, q0+kk): staged (ii, jj, kk+1)
+        {
+            int s = si(ii, jj, kk + 1);
+            T kw = ld<T, C>(K_w, L.off(c0 - 1 + ii, r0 - 1 + jj, q0 + kk));
+            sm.zw[e] = kw * ((sm.W[s] - sm.W[s - SM::SX * SM::SY]) + (sm.Nxz[s] - sm.Nxz[s + 1]) +
+                             (sm.Nyz[s] - sm.Nyz[s + SM::SX]));
+        }
+    }
+    __syncthreads();
+    auto zi = [](int ii, int jj, int kk) { return (kk * SM::ZY + jj) * SM::ZX + ii; };
+    Acc<T> acc;
+    const int tx = t & (TX - 1);
+    for (int rep = 0; rep < 2; ++rep) {
+        int lin = (t >> 5) + rep * 8;          // 16 rows of 32 per tile
+        int ty = lin % TY3, tz = lin / TY3;
+        int64_t o = L.off(c0 + tx, r0 + ty, q0 + tz);
+        T v[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) v[f] = MODE == MODE_CG ? pnew[f * S + o] : x[f * S + o];
+        // z_u(c, r, q): index (tx, ty+1, tz+1); z_u(c+1): (tx+1, ...)
+        T zu = sm.zu[zi(tx, ty + 1, tz + 1)], zu_cp = sm.zu[zi(tx + 1, ty + 1, tz + 1)];
+        T zu_rm = sm.zu[zi(tx, ty, tz + 1)], zu_qm = sm.zu[zi(tx, ty + 1, tz)];
+        // z_v(c, r, q): (tx+1, ty, tz+1)
+        T zv = sm.zv[zi(tx + 1, ty, tz + 1)], zv_rp = sm.zv[zi(tx + 1, ty + 1, tz + 1)];
+        T zv_cm = sm.zv[zi(tx, ty, tz + 1)], zv_qm = sm.zv[zi(tx + 1, ty, tz)];
+        // z_w(c, r, q): (tx+1, ty+1, tz)
+        T zw = sm.zw[zi(tx + 1, ty + 1, tz)], zw_qp = sm.zw[zi(tx + 1, ty + 1, tz + 1)];
+        T zw_cm = sm.zw[zi(tx, ty + 1, tz)], zw_rm = sm.zw[zi(tx + 1, ty, tz)];
+        T ac = ld<T, C>(a_c, o), dc = ld<T, C>(d_c, o);
+        T yv[6];
+        if (ac != T(0)) {
+            T ww = zw - zw_qp;
+            yv[5] = ac * ((zu - zu_cp) + (zv - zv_rp) + ww);
+            yv[0] = dc * (v[0] + T(0.5) * v[1]) + ac * ((zu_cp - zu) + ww);
+            yv[1] = dc * (v[1] + T(0.5) * v[0]) + ac * ((zv_rp - zv) + ww);
+        } else {
+            yv[5] = v[5]; yv[0] = v[0]; yv[1] = v[1];
+        }
+        yv[2] = ld<T, C>(d_xy, o) * v[2] + ld<T, C>(a_xy, o) * ((zu - zu_rm) + (zv - zv_cm));
+        yv[3] = ld<T, C>(d_xz, o) * v[3] + ld<T, C>(a_xz, o) * ((zu - zu_qm) + (zw - zw_cm));
+        yv[4] = ld<T, C>(d_yz, o) * v[4] + ld<T, C>(a_yz, o) * ((zv - zv_qm) + (zw - zw_rm));
+        if (MODE == MODE_RESID) {
+            const T* b = (const T*)args.b;
+#pragma unroll
+            for (int f = 0; f < 6; ++f) yv[f] = b[f * S + o] - yv[f];
+        }
+#pragma unroll
+        for (int f = 0; f < 6; ++f) y[f * S + o] = yv[f];
+        if (MODE == MODE_RESID) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) acc.add(yv[f], yv[f]);
+        } else if (MODE == MODE_CG) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) acc.add(v[f], yv[f]);
+        }
+    }
+    if (MODE != MODE_PLAIN) {
+        double v = acc.warp();
+        if ((t & 31) != 0) v = 0.0;
+        CgScalars* sc = args.sc;
+        block_partial_and_finish<256>(v, args.partial, args.counter, nblocks, [&](double tot) {
+            if (MODE == MODE_RESID) { sc->rr = tot; return; }
+            sc->pq = tot;
+            if (!(tot > 0.0) || !isfinite(tot)) { sc->done = 1; sc->status = (isfinite(tot) ? STOKES_ERR_BREAKDOWN : STOKES_ERR_NONFINITE); }
+            else sc->alpha = sc->rz / tot;
+        });
+    }
+}
+
+template <class T, class C, int MODE>
+static cudaError_t launch_mode(const Layout& L, const int* tiles, int ntiles, const Coef<C>& cf, const T* x, T* y,
+                               const ApplyArgs& a, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    if (L.dim == 2) {
+        k_apply2d<T, C, MODE><<<ntiles, 256, 0, s>>>(L, tiles, cf, x, y, a, ntiles);
+    } else {
+        size_t sm = sizeof(Smem3<T>);
+        k_apply3d<T, C, MODE><<<ntiles, 256, sm, s>>>(L, tiles, cf, x, y, a, ntiles);
+    }
+    return cudaGetLastError();
+}
+
+template <class T, class C>
+cudaError_t launch_apply_mode(const Layout& L, const int* tiles, int ntiles, const Coef<C>& cf, const T* x, T* y,
+                              int mode, const ApplyArgs& a, cudaStream_t s) {
+    switch (mode) {
+        case MODE_PLAIN: return launch_mode<T, C, MODE_PLAIN>(L, tiles, ntiles, cf, x, y, a, s);
+        case MODE_RESID: return launch_mode<T, C, MODE_RESID>(L, tiles, ntiles, cf, x, y, a, s);
+        default: return launch_mode<T, C, MODE_CG>(L, tiles, ntiles, cf, x, y, a, s);
+    }
+}
+
+template <class T, class C>
+static void set_attr3() {
+    int sm = (int)sizeof(Smem3<T>);
+    cudaFuncSetAttribute(k_apply3d<T, C, MODE_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_apply3d<T, C, MODE_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_apply3d<T, C, MODE_CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
+// Opt the 3D kernels into more than 48 KB of dynamic shared memory (once per
+// process and device, before any launch or graph capture).
+void apply_set_attributes() {
+    set_attr3<double, double>();
+    set_attr3<float, float>();
+    set_attr3<float, __nv_bfloat16>();
+}
+
+template cudaError_t launch_apply_mode<double, double>(const Layout&, const int*, int, const Coef<double>&,
+                                                       const double*, double*, int, const ApplyArgs&, cudaStream_t);
+template cudaError_t launch_apply_mode<float, float>(const Layout&, const int*, int, const Coef<float>&, const float*,
+                                                     float*, int, const ApplyArgs&, cudaStream_t);
+template cudaError_t launch_apply_mode<float, __nv_bfloat16>(const Layout&, const int*, int,
+                                                             const Coef<__nv_bfloat16>&, const float*, float*, int,
+                                                             const ApplyArgs&, cudaStream_t);
+
+}  // namespace stk

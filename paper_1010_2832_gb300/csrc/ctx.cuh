@@ -1,0 +1,96 @@
+// Context of one grid: layout, device arrays and solver work space.
+#pragma once
+#include <string>
+#include <vector>
+#include "internal.cuh"
+
+namespace stk {
+
+struct Ptr3 { const double* p[3]; };
+struct Ptr4 { const double* p[4]; };
+
+// Device pointers handed to the build kernels (plain struct, passed by value).
+struct DevArrays {
+    double* WL[7];
+    double* WF[7];
+    uint8_t* fflag[3];
+    double* effWF[3];
+    double* K64[3];
+    double* rec[3];       // dt / (rho W_L) on live faces (velocity recovery)
+    double* ubc[3];
+    uint8_t* act[4];      // activity of unknown sites: cell, then stress sites
+    double* coef64;
+    float* coef32;
+    __nv_bfloat16* coef16;
+    double* minv64;
+    float* minv32;
+    uint8_t* tile_flag;
+};
+
+// Work vectors of one precision.
+template <class T> struct CgWork {
+    T *x = nullptr, *r = nullptr, *z = nullptr, *p[2] = {nullptr, nullptr}, *q = nullptr;
+};
+
+struct Ctx {
+    stokes_grid g{};
+    Layout L{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    int nf = 0;        // unknown fields
+    int nk = 0;        // sample kinds
+    int nd = 0;        // face kinds
+    int nsite = 0;     // unknown sites (cell + stress sites)
+    int ncoef = 0;
+    int ntiles_all = 0;
+    int ntiles_active = 0;
+    int* tiles = nullptr;       // active tile list (device)
+    int* d_ntiles = nullptr;
+    bool have_weights = false;
+    bool own_stream = false;
+    std::vector<void*> allocs;
+    DevArrays A{};
+    void* weight_block = nullptr;
+    size_t weight_bytes = 0;
+    // solver state
+    CgScalars* sc = nullptr;     // [0] inner/plain CG, [1] outer
+    CgScalars* h_sc = nullptr;   // pinned host mirror
+    double* partial = nullptr;   // per-block partials (2 arrays)
+    unsigned* counter = nullptr;
+    CgWork<double> w64;
+    CgWork<float> w32;
+    double* b64 = nullptr;       // rhs (solve_step)
+    double* x64 = nullptr;       // solution (solve_step)
+    double* y64 = nullptr;       // scratch
+    cudaEvent_t ev[4]{};
+    double last_apply_ms = -1.0;
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // inner solve per precision
+
+    DevArrays dev_arrays() const { return A; }
+    cudaError_t zero_weights() { return cudaMemsetAsync(weight_block, 0, weight_bytes, stream); }
+    template <class C> Coef<C> coef() const;
+    int64_t vec_elems() const { return (int64_t)nf * L.stride; }
+};
+
+template <> inline Coef<double> Ctx::coef<double>() const {
+    Coef<double> c{};
+    for (int f = 0; f < ncoef; ++f) c.f[f] = A.coef64 + (int64_t)f * L.stride;
+    return c;
+}
+template <> inline Coef<float> Ctx::coef<float>() const {
+    Coef<float> c{};
+    for (int f = 0; f < ncoef; ++f) c.f[f] = A.coef32 + (int64_t)f * L.stride;
+    return c;
+}
+template <> inline Coef<__nv_bfloat16> Ctx::coef<__nv_bfloat16>() const {
+    Coef<__nv_bfloat16> c{};
+    for (int f = 0; f < ncoef; ++f) c.f[f] = A.coef16 + (int64_t)f * L.stride;
+    return c;
+}
+
+template <class T, class C>
+cudaError_t launch_apply_mode(const Layout& L, const int* tiles, int ntiles, const Coef<C>& cf, const T* x, T* y,
+                              int mode, const ApplyArgs& a, cudaStream_t s);
+
+}  // namespace stk

@@ -1,0 +1,374 @@
+// Preconditioned conjugate gradients on the SPD pressure-stress system and
+// the FP64 iterative-refinement driver around it.
+//
+// Inner solve (precision T of the vectors, C of the coefficients), Jacobi
+// preconditioner M^-1 = diag(A)^-1:
+//   init      r = T(scale * r64), z = M^-1 r, x = 0, p_old = 0, rho = r.z
+//   iterate   [apply, CG mode]  p = z + beta p_old, q = A p, alpha = rho / p.q
+//             [update]          x += alpha p, r -= alpha q, z = M^-1 r,
+//                               rho' = r.z, beta = rho'/rho, stop on r.r <= tol2
+// The loop runs on the device as a CUDA graph with a conditional while node
+// whose condition the update kernel clears when the solve is done, so the
+// host is involved once per inner solve.
+//
+// Outer loop (FP64): x64 += d / scale, r64 = b - A64 x64 recomputed from
+// scratch with the FP64 operator; stop when ||r64|| <= tol ||b||.  In FP64
+// mode the inner solve is FP64 CG and normally one outer step suffices.
+#include <cmath>
+#include <cstring>
+#include <vector>
+#include "internal.cuh"
+#include "ctx.cuh"
+
+namespace stk {
+
+// Walk the slots of one tile: 2D 8 rows of 32, 3D 16 rows of 32.
+__device__ __forceinline__ int tile_rows(const Layout& L) { return L.dim == 2 ? TY2 : TY3 * TZ3; }
+
+__device__ __forceinline__ int64_t tile_row_off(const Layout& L, int tile, int row) {
+    int tcx = tile % L.ntx;
+    if (L.dim == 2) {
+        int tr = tile / L.ntx;
+        return L.off(tcx * TX, tr * TY2 + row, 0);
+    }
+    int rest = tile / L.ntx;
+    int tr = rest % L.nty, tq = rest / L.nty;
+    return L.off(tcx * TX, tr * TY3 + row % TY3, tq * TZ3 + row / TY3);
+}
+
+template <class T> struct AccT;
+template <> struct AccT<double> {
+    double s = 0.0;
+    __device__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ double warp() { return warp_sum(s); }
+};
+template <> struct AccT<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ void add(float a, float b) {
+        float p = a * b;
+        float e = fmaf(a, b, -p);
+        float s, t;
+        two_sum(hi, p, s, t);
+        lo += t + e;
+        hi = s;
+    }
+    __device__ double warp() { return warp_sum_ff(hi, lo); }
+};
+
+// Two partial sums per block; the last block to finish reduces both.
+template <class Fin>
+__device__ void block_partial2(double v0, double v1, double* partial, unsigned* counter, int nblocks, Fin fin) {
+    __shared__ double red[2][8];
+    __shared__ bool last;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { red[0][w] = v0; red[1][w] = v1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int q = 0; q < 8; ++q) { s0 += red[0][q]; s1 += red[1][q]; }
+        partial[2 * blockIdx.x] = s0;
+        partial[2 * blockIdx.x + 1] = s1;
+        __threadfence();
+        unsigned prev = atomicAdd(counter, 1u);
+        last = (prev == (unsigned)nblocks - 1u);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s0 = 0.0, s1 = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 256) {
+        s0 += ((volatile double*)partial)[2 * b];
+        s1 += ((volatile double*)partial)[2 * b + 1];
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    __syncthreads();
+    if (lane == 0) { red[0][w] = s0; red[1][w] = s1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0;
+        for (int q = 0; q < 8; ++q) { t0 += red[0][q]; t1 += red[1][q]; }
+        fin(t0, t1);
+        *counter = 0u;
+    }
+}
+
+// init: r = T(scale * r64), z = minv r, x = 0, p0 = 0; rho = r.z, rr0 = r.r
+template <class T>
+__global__ void __launch_bounds__(256) k_cg_init(Layout L, const int* __restrict__ tiles, int nf, const double* r64,
+                                                 const T* __restrict__ minv, CgWork<T> w, CgScalars* sc,
+                                                 double* partial, unsigned* counter, int nblocks,
+                                                 cudaGraphConditionalHandle h) {
+    const int tile = tiles[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const T scale = (T)sc->scale;
+    AccT<T> rz, rr;
+    const int nrow = tile_rows(L);
+    for (int row = warp; row < nrow; row += 8) {
+        int64_t o = tile_row_off(L, tile, row) + lane;
+        for (int f = 0; f < nf; ++f) {
+            int64_t of = (int64_t)f * L.stride + o;
+            T r = (T)(r64[of] * (double)scale);
+            T z = minv[of] * r;
+            w.r[of] = r; w.z[of] = z; w.x[of] = T(0); w.p[0][of] = T(0);
+            rz.add(r, z); rr.add(r, r);
+        }
+    }
+    double a = rz.warp(), b = rr.warp();
+    block_partial2(a, b, partial, counter, nblocks, [&](double trz, double trr) {
+        sc->rz = trz; sc->rr = trr; sc->rr0 = trr;
+        sc->tol2 = sc->tol_rel * sc->tol_rel * trr;
+        sc->beta = 0.0; sc->iter = 0; sc->status = 0;
+        sc->done = (trr <= sc->tol2 || trr == 0.0) ? 1 : 0;
+        if (!isfinite(trr)) { sc->done = 1; sc->status = STOKES_ERR_NONFINITE; }
+        cudaGraphSetConditional(h, sc->done ? 0u : 1u);
+    });
+}
+
+// update: x += alpha p, r -= alpha q, z = minv r; rho' = r.z, r.r
+template <class T>
+__global__ void __launch_bounds__(256) k_cg_update(Layout L, const int* __restrict__ tiles, int nf,
+                                                   const T* __restrict__ minv, CgWork<T> w, const T* __restrict__ p,
+                                                   CgScalars* sc, double* partial, unsigned* counter, int nblocks,
+                                                   cudaGraphConditionalHandle h) {
+    if (sc->done) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+        return;
+    }
+    const int tile = tiles[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const T alpha = (T)sc->alpha;
+    AccT<T> rz, rr;
+    const int nrow = tile_rows(L);
+    for (int row = warp; row < nrow; row += 8) {
+        int64_t o = tile_row_off(L, tile, row) + lane;
+        for (int f = 0; f < nf; ++f) {
+            int64_t of = (int64_t)f * L.stride + o;
+            T pv = p[of];
+            w.x[of] += alpha * pv;
+            T r = w.r[of] - alpha * w.q[of];
+            T z = minv[of] * r;
+            w.r[of] = r; w.z[of] = z;
+            rz.add(r, z); rr.add(r, r);
+        }
+    }
+    double a = rz.warp(), b = rr.warp();
+    block_partial2(a, b, partial, counter, nblocks, [&](double trz, double trr) {
+        sc->rr = trr;
+        sc->iter += 1;
+        if (!isfinite(trr) || !isfinite(trz)) { sc->done = 1; sc->status = STOKES_ERR_NONFINITE; }
+        else if (trr <= sc->tol2) { sc->done = 1; }
+        else if (!(trz > 0.0)) { sc->done = 1; sc->status = STOKES_ERR_BREAKDOWN; }
+        else if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = STOKES_ERR_NOT_CONVERGED; }
+        sc->beta = trz / sc->rz;
+        sc->rz = trz;
+        cudaGraphSetConditional(h, sc->done ? 0u : 1u);
+    });
+}
+
+// x64 += x / scale (refinement update), over active tiles
+template <class T>
+__global__ void __launch_bounds__(256) k_ir_update(Layout L, const int* __restrict__ tiles, int nf, double* x64,
+                                                   const T* __restrict__ d, const CgScalars* sc) {
+    const int tile = tiles[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double inv = 1.0 / sc->scale;
+    const int nrow = tile_rows(L);
+    for (int row = warp; row < nrow; row += 8) {
+        int64_t o = tile_row_off(L, tile, row) + lane;
+        for (int f = 0; f < nf; ++f) {
+            int64_t of = (int64_t)f * L.stride + o;
+            x64[of] += (double)d[of] * inv;
+        }
+    }
+}
+
+// r64 = b, x64 = 0 over active tiles; rr = b.b (FP64)
+__global__ void __launch_bounds__(256) k_outer_init(Layout L, const int* __restrict__ tiles, int nf, const double* b,
+                                                    double* x64, double* r64, CgScalars* so, double* partial,
+                                                    unsigned* counter, int nblocks) {
+    const int tile = tiles[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double s = 0.0;
+    const int nrow = tile_rows(L);
+    for (int row = warp; row < nrow; row += 8) {
+        int64_t o = tile_row_off(L, tile, row) + lane;
+        for (int f = 0; f < nf; ++f) {
+            int64_t of = (int64_t)f * L.stride + o;
+            double v = b[of];
+            r64[of] = v; x64[of] = 0.0;
+            s = fma(v, v, s);
+        }
+    }
+    double a = warp_sum(s);
+    block_partial2(a, 0.0, partial, counter, nblocks, [&](double t0, double) {
+        so->rr = t0; so->rr0 = t0; so->iter = 0; so->status = 0; so->done = 0;
+    });
+}
+
+// Build the inner-solve graph for one precision: init kernel, then a
+// conditional while node whose body runs two CG iterations (the search
+// direction alternates between p[0] and p[1]).
+template <class T, class C>
+static cudaError_t build_inner_graph(Ctx* c, CgWork<T>& w, const T* minv, const Coef<C>& cf, CgScalars* sc,
+                                     cudaGraphExec_t* out) {
+    const Layout& L = c->L;
+    cudaStream_t s = c->stream;
+    const int nb = c->ntiles_active;
+    double* part = c->partial;
+    unsigned* cnt = c->counter;
+    cudaError_t e;
+    cudaGraph_t g = nullptr;
+    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+    // init node by capture into g
+    if ((e = cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+        return e;
+    k_cg_init<T><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, c->w64.r, minv, w, sc, part, cnt, nb, h);
+    cudaGraph_t captured = nullptr;
+    if ((e = cudaStreamEndCapture(s, &captured)) != cudaSuccess) return e;
+    // find the init node (the graph's only node so far)
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cond;
+    if ((e = cudaGraphAddNode(&cond, g, nodes.data(), nullptr, nn, &cp)) != cudaSuccess) return e;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+        return e;
+    for (int k = 0; k < 2; ++k) {
+        ApplyArgs a{};
+        a.pold = w.p[k];
+        a.pnew = w.p[k ^ 1];
+        a.partial = part;
+        a.counter = cnt;
+        a.sc = sc;
+        launch_apply_mode<T, C>(L, c->tiles, nb, cf, w.z, w.q, MODE_CG, a, s);
+        k_cg_update<T><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, minv, w, w.p[k ^ 1], sc, part, cnt, nb, h);
+    }
+    cudaGraph_t cap2 = nullptr;
+    if ((e = cudaStreamEndCapture(s, &cap2)) != cudaSuccess) return e;
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+template <class T, class C>
+static cudaError_t run_inner(Ctx* c, int prec_slot, CgWork<T>& w, const T* minv, const Coef<C>& cf) {
+    cudaGraphExec_t& ge = c->graph[prec_slot];
+    cudaError_t e;
+    if (!ge) {
+        if ((e = build_inner_graph<T, C>(c, w, minv, cf, c->sc, &ge)) != cudaSuccess) return e;
+    }
+    return cudaGraphLaunch(ge, c->stream);
+}
+
+static cudaError_t fetch_scalars(Ctx* c) {
+    cudaError_t e = cudaMemcpyAsync(c->h_sc, c->sc, 2 * sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(c->stream);
+}
+
+static cudaError_t push_inner_params(Ctx* c, double scale, double tol_rel, int max_iter) {
+    CgScalars& h = c->h_sc[0];
+    std::memset(&h, 0, sizeof(h));
+    h.scale = scale;
+    h.tol_rel = tol_rel;
+    h.max_iter = max_iter;
+    return cudaMemcpyAsync(c->sc, &h, sizeof(CgScalars), cudaMemcpyHostToDevice, c->stream);
+}
+
+stokes_status solve_system(Ctx* c, const double* b, double* x, const stokes_options* o, stokes_stats* st) {
+    const Layout& L = c->L;
+    cudaStream_t s = c->stream;
+    const int nb = c->ntiles_active;
+    cudaError_t e = cudaSuccess;
+    int total_iter = 0, outer = 0;
+    int status = STOKES_OK;
+    double rel = 0.0;
+#define CK(...)                                                                \
+    do {                                                                       \
+        if ((e = (__VA_ARGS__)) != cudaSuccess) {                              \
+            set_error(c, std::string("CUDA error in solve: ") + cudaGetErrorString(e)); \
+            return STOKES_ERR_CUDA;                                            \
+        }                                                                      \
+    } while (0)
+    if (nb == 0) {
+        if (st) { st->iterations = 0; st->outer = 0; st->rel_residual = 0.0; st->status = 0; }
+        return STOKES_OK;
+    }
+    CgScalars* so = c->sc + 1;
+    k_outer_init<<<nb, 256, 0, s>>>(L, c->tiles, c->nf, b, x, c->w64.r, so, c->partial, c->counter, nb);
+    CK(cudaGetLastError());
+    CK(fetch_scalars(c));
+    const double bb = c->h_sc[1].rr0;
+    if (bb == 0.0) {
+        if (st) { st->iterations = 0; st->outer = 0; st->rel_residual = 0.0; st->status = 0; }
+        return STOKES_OK;
+    }
+    if (!std::isfinite(bb)) {
+        set_error(c, "non-finite right-hand side");
+        return STOKES_ERR_NONFINITE;
+    }
+    double rr = bb;
+    const int mode = o->mode;
+    for (outer = 0; outer < o->max_outer; ++outer) {
+        rel = std::sqrt(rr / bb);
+        if (rel <= o->tol) break;
+        int remaining = o->max_iter - total_iter;
+        if (remaining <= 0) { status = STOKES_ERR_NOT_CONVERGED; break; }
+        // inner tolerance: loose in mixed mode, the final target in FP64 mode
+        double target = 0.5 * o->tol / rel;   // relative to the current residual
+        double tol_rel = mode == STOKES_FP64 ? target : std::fmax(o->inner_tol, target);
+        double scale = 1.0 / std::sqrt(rr);
+        CK(push_inner_params(c, scale, tol_rel, remaining));
+        if (mode == STOKES_FP64) {
+            CK(run_inner<double, double>(c, 0, c->w64, c->A.minv64, c->coef<double>()));
+            k_ir_update<double><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, x, c->w64.x, c->sc);
+        } else if (mode == STOKES_FP32) {
+            CK(run_inner<float, float>(c, 1, c->w32, c->A.minv32, c->coef<float>()));
+            k_ir_update<float><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, x, c->w32.x, c->sc);
+        } else {
+            CK(run_inner<float, __nv_bfloat16>(c, 2, c->w32, c->A.minv32, c->coef<__nv_bfloat16>()));
+            k_ir_update<float><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, x, c->w32.x, c->sc);
+        }
+        CK(cudaGetLastError());
+        // true residual in FP64: r64 = b - A64 x
+        ApplyArgs a{};
+        a.b = b;
+        a.partial = c->partial;
+        a.counter = c->counter;
+        a.sc = so;
+        CK(launch_apply_mode<double, double>(L, c->tiles, nb, c->coef<double>(), x, c->w64.r, MODE_RESID, a, s));
+        CK(fetch_scalars(c));
+        total_iter += c->h_sc[0].iter;
+        rr = c->h_sc[1].rr;
+        int ist = c->h_sc[0].status;
+        if (!std::isfinite(rr)) { status = STOKES_ERR_NONFINITE; break; }
+        if (ist == STOKES_ERR_NONFINITE || ist == STOKES_ERR_BREAKDOWN) {
+            // breakdown of the inner solve: keep the refined x if it helped
+            if (std::sqrt(rr / bb) > o->tol) { status = ist; rel = std::sqrt(rr / bb); break; }
+        }
+    }
+    rel = std::sqrt(rr / bb);
+    if (status == STOKES_OK && rel > o->tol) status = STOKES_ERR_NOT_CONVERGED;
+    if (st) {
+        st->iterations = total_iter;
+        st->outer = outer;
+        st->rel_residual = rel;
+        st->status = status;
+    }
+    if (status != STOKES_OK) set_error(c, "solve stopped with status " + std::to_string(status) +
+                                              " at relative residual " + std::to_string(rel));
+    return (stokes_status)status;
+#undef CK
+}
+
+}  // namespace stk

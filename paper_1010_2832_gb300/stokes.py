@@ -1,0 +1,243 @@
+"""Thin Python binding of libstokes (include/stokes.h) over ctypes.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device arrays are torch CUDA tensors (float64 unless stated), whose
+data pointers are handed to the C entry points; the context's stream is the
+torch stream current at creation.  There is no CPU fallback: importing
+without the built library raises.
+"""
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstokes.so")
+
+FP64, FP32, BF16 = 0, 1, 2
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_NOT_CONVERGED", -4: "ERR_BREAKDOWN",
+          -5: "ERR_TIMEOUT", -6: "ERR_BOUNDS", -7: "ERR_NONFINITE", -8: "ERR_STATE"}
+
+
+class Grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("h", C.c_double), ("dt", C.c_double), ("origin", C.c_double * 3)]
+
+
+class Layout(C.Structure):
+    _fields_ = [("nfields", C.c_int), ("field_stride", C.c_int64), ("base", C.c_int64),
+                ("pitch", C.c_int), ("rows", C.c_int), ("planes", C.c_int), ("total", C.c_int64)]
+
+
+class Options(C.Structure):
+    _fields_ = [("mode", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("inner_tol", C.c_double),
+                ("max_outer", C.c_int), ("check_every", C.c_int), ("precond", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("outer", C.c_int), ("rel_residual", C.c_double),
+                ("ms_rhs", C.c_double), ("ms_solve", C.c_double), ("ms_recover", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTED = ("stokes_create", "stokes_destroy", "stokes_last_error", "stokes_build_weights", "stokes_vector_layout",
+            "stokes_apply", "stokes_rhs", "stokes_recover", "stokes_default_options", "stokes_solve_step",
+            "stokes_solve_system", "stokes_export", "stokes_export_size", "stokes_slots_to_fields",
+            "stokes_fields_to_slots", "stokes_last_apply_ms")
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libstokes.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libstokes.so not found at {path}: run paper_1010_2832_gb300.build.build()")
+    lib = C.CDLL(path)
+    P, I, D, I64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+    PP = C.POINTER(C.c_void_p)
+    sig = {
+        "stokes_create": (I, [C.POINTER(P), C.POINTER(Grid), P]),
+        "stokes_destroy": (I, [P]),
+        "stokes_last_error": (C.c_char_p, [P]),
+        "stokes_build_weights": (I, [P, P, P, PP, PP, PP]),
+        "stokes_vector_layout": (I, [P, C.POINTER(Layout)]),
+        "stokes_apply": (I, [P, P, P, I]),
+        "stokes_rhs": (I, [P, PP, P]),
+        "stokes_recover": (I, [P, PP, P, PP]),
+        "stokes_default_options": (None, [C.POINTER(Options)]),
+        "stokes_solve_step": (I, [P, PP, PP, PP, P, C.POINTER(Options), C.POINTER(Stats)]),
+        "stokes_solve_system": (I, [P, P, P, C.POINTER(Options), C.POINTER(Stats)]),
+        "stokes_export": (I, [P, I, P]),
+        "stokes_export_size": (I64, [P, I]),
+        "stokes_slots_to_fields": (I, [P, P, P]),
+        "stokes_fields_to_slots": (I, [P, P, P]),
+        "stokes_last_apply_ms": (D, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptrs(tensors):
+    arr = (C.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+    return C.cast(arr, C.POINTER(C.c_void_p)), arr
+
+
+def _dev(t, dtype=torch.float64):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA tensor of dtype %s" % dtype)
+    return t
+
+
+class StokesError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def default_options(**kw):
+    lib = load_library()
+    o = Options()
+    lib.stokes_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class StokesContext:
+    """One grid on the current CUDA device (see include/stokes.h)."""
+
+    def __init__(self, dim, n, h, dt, origin=(0.0, 0.0, 0.0), stream=None):
+        self.lib = load_library()
+        g = Grid()
+        g.dim = dim
+        g.nx, g.ny = n[0], n[1]
+        g.nz = n[2] if dim == 3 else 0
+        g.h, g.dt = h, dt
+        for d in range(3):
+            g.origin[d] = origin[d] if d < len(origin) else 0.0
+        self.dim, self.n = dim, tuple(n)
+        # None: the library makes its own stream, ordered with torch's
+        # (legacy) default stream; a torch.cuda.Stream is used as given
+        self.stream = stream
+        h_ = C.c_void_p()
+        sp = None if stream is None else C.c_void_p(stream.cuda_stream)
+        st = self.lib.stokes_create(C.byref(h_), C.byref(g), sp)
+        if st != 0:
+            raise StokesError(st, self.lib.stokes_last_error(None).decode())
+        self.h = h_
+        lay = Layout()
+        self.lib.stokes_vector_layout(self.h, C.byref(lay))
+        self.layout = lay
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.stokes_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != 0:
+            raise StokesError(st, self.lib.stokes_last_error(self.h).decode())
+        return st
+
+    # ---- weights ---------------------------------------------------------
+    def build_weights(self, phi_liquid, phi_solid, rho, mu, u_bc):
+        rp, ra = _ptrs([_dev(t) for t in rho])
+        mp, ma = _ptrs([_dev(t) for t in mu])
+        up, ua = _ptrs([_dev(t) for t in u_bc])
+        self._check(self.lib.stokes_build_weights(self.h, _dev(phi_liquid).data_ptr(), _dev(phi_solid).data_ptr(),
+                                                  rp, mp, up))
+
+    # ---- vectors -----------------------------------------------------------
+    def new_vector(self, dtype=torch.float64):
+        return torch.zeros(self.layout.total, dtype=dtype, device="cuda")
+
+    def apply(self, x, y, precision=FP64):
+        dt = torch.float64 if precision == FP64 else torch.float32
+        self._check(self.lib.stokes_apply(self.h, _dev(x, dt).data_ptr(), _dev(y, dt).data_ptr(), precision))
+
+    def last_apply_ms(self):
+        return self.lib.stokes_last_apply_ms(self.h)
+
+    def rhs(self, u_star, b):
+        up, ua = _ptrs([_dev(t) for t in u_star])
+        self._check(self.lib.stokes_rhs(self.h, up, _dev(b).data_ptr()))
+
+    def recover(self, u_star, x, u_out):
+        up, ua = _ptrs([_dev(t) for t in u_star])
+        op, oa = _ptrs([_dev(t) for t in u_out])
+        self._check(self.lib.stokes_recover(self.h, up, _dev(x).data_ptr(), op))
+
+    def solve_system(self, b, x, options=None):
+        o = options or default_options()
+        st = Stats()
+        rc = self.lib.stokes_solve_system(self.h, _dev(b).data_ptr(), _dev(x).data_ptr(), C.byref(o), C.byref(st))
+        if rc not in (0, -3):
+            self._check(rc)
+        return st
+
+    def solve_step(self, u_star, u_out, tau_out, p_out, options=None):
+        o = options or default_options()
+        st = Stats()
+        up, ua = _ptrs([_dev(t) for t in u_star])
+        op, oa = _ptrs([_dev(t) for t in u_out])
+        tp, ta = _ptrs([_dev(t) for t in tau_out])
+        rc = self.lib.stokes_solve_step(self.h, up, op, tp, _dev(p_out).data_ptr(), C.byref(o), C.byref(st))
+        if rc not in (0, -3):
+            self._check(rc)
+        return st
+
+    def export(self, what):
+        n = self.lib.stokes_export_size(self.h, what)
+        buf = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        self._check(self.lib.stokes_export(self.h, what, buf.data_ptr()))
+        return buf.view(torch.float64) if what in (0, 1) else buf
+
+    def slots_to_fields(self, slots):
+        n = self.field_vector_length()
+        out = torch.zeros(n, dtype=torch.float64, device="cuda")
+        self._check(self.lib.stokes_slots_to_fields(self.h, _dev(slots).data_ptr(), out.data_ptr()))
+        return out
+
+    def fields_to_slots(self, fields):
+        out = self.new_vector()
+        self._check(self.lib.stokes_fields_to_slots(self.h, _dev(fields).data_ptr(), out.data_ptr()))
+        return out
+
+    def field_vector_length(self):
+        nx, ny = self.n[0], self.n[1]
+        if self.dim == 2:
+            return 2 * nx * ny + (nx + 1) * (ny + 1)
+        nz = self.n[2]
+        return (3 * nx * ny * nz + nz * (ny + 1) * (nx + 1) + (nz + 1) * ny * (nx + 1)
+                + (nz + 1) * (ny + 1) * nx)
+
+
+def upload_workload(wl):
+    """Copy a ``workloads.Workload`` to CUDA tensors: dict of lists."""
+    t = lambda a: torch.from_numpy(a).to("cuda").contiguous()
+    return dict(phi_liquid=t(wl.phi_liquid), phi_solid=t(wl.phi_solid), rho=[t(a) for a in wl.rho],
+                mu=[t(a) for a in wl.mu], u_bc=[t(a) for a in wl.u_bc], u_star=[t(a) for a in wl.u_star])
+
+
+def context_for(wl, stream=None):
+    """Create a context for a workload and build its weights on the device."""
+    ctx = StokesContext(wl.dim, wl.n, wl.h, wl.dt, wl.origin, stream=stream)
+    d = upload_workload(wl)
+    ctx.build_weights(d["phi_liquid"], d["phi_solid"], d["rho"], d["mu"], d["u_bc"])
+    return ctx, d
