@@ -166,6 +166,10 @@ typedef struct {
     int max_outer;     /* cap on refinement steps (mixed)                    */
     int check_every;   /* iterations between host convergence checks        */
     int precond;       /* 0 = Jacobi (point diagonal)                        */
+    int use_graph;     /* 1: CG loop in a device-side CUDA graph (conditional
+                          while node); 0: host-driven chunks of check_every
+                          iterations launched one kernel at a time (for
+                          profilers that cannot enter conditional graphs)   */
 } stokes_options;
 
 typedef struct {
@@ -174,6 +178,10 @@ typedef struct {
     int outer;               /* refinement steps (mixed), 1 for FP64 PCG    */
     double rel_residual;     /* final true relative residual in FP64        */
     double ms_rhs, ms_solve, ms_recover;  /* device time per phase          */
+    int precision_used;      /* inner precision of the last refinement step:
+                                a refinement step that does not reduce the
+                                FP64 residual is undone and the inner solve
+                                moves up one precision (BF16 -> FP32 -> FP64) */
 } stokes_stats;
 
 /* Fill ``o`` with defaults: FP64 mode, tol 1e-8, max_iter 200000,
@@ -220,6 +228,20 @@ stokes_status stokes_fields_to_slots(stokes_ctx ctx, const double* fields, doubl
 /* Device time (ms) of the last stokes_apply call, measured with CUDA events
  * on the context's stream (synchronises).  Returns -1 if none. */
 double stokes_last_apply_ms(stokes_ctx ctx);
+
+/* Measurement support: run ``launches`` real CG iterations (right-hand side
+ * = the last one stokes_solve_step built, Jacobi, inner precision
+ * ``precision``) launch by launch, outside any graph, with CUDA events
+ * around each kernel on the context's stream; return the mean device time
+ * (ms) of the CG-mode apply kernel (direction update, A p and p.Ap fused)
+ * and of the vector-update kernel.  Overwrites the solver's work vectors.
+ * Synchronises. */
+stokes_status stokes_bench_cg_kernels(stokes_ctx ctx, int precision, int launches, double* ms_apply,
+                                      double* ms_update);
+
+/* Number of tiles holding an active unknown (2D tiles are 32 x 8 slots,
+ * 3D tiles 32 x 4 x 4); every CG kernel launches one CTA per such tile. */
+int stokes_active_tiles(stokes_ctx ctx);
 
 #ifdef __cplusplus
 }

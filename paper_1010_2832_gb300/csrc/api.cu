@@ -17,7 +17,24 @@ namespace stk {
 void set_error(Ctx* c, const std::string& m) { c->err = m; }
 cudaError_t launch_unpack(Ctx* c, const double* slots, double* const* fields, int to_fields);
 void apply_set_attributes();
+cudaError_t bench_cg_kernels(Ctx* c, int precision, int launches, double* ms_apply, double* ms_update);
 }  // namespace stk
+
+extern "C" stokes_status stokes_bench_cg_kernels(stokes_ctx h, int precision, int launches, double* ms_apply,
+                                                 double* ms_update) {
+    if (!h || !ms_apply || !ms_update || launches < 1 || precision < 0 || precision > 2) return STOKES_ERR_ARG;
+    Ctx& c = h->c;
+    if (!c.have_weights) { c.err = "stokes_build_weights has not run"; return STOKES_ERR_STATE; }
+    if (c.ntiles_active == 0) { c.err = "no active unknowns"; return STOKES_ERR_STATE; }
+    cudaError_t e = bench_cg_kernels(&c, precision, launches, ms_apply, ms_update);
+    if (e != cudaSuccess) {
+        c.err = std::string("kernel timing failed: ") + cudaGetErrorString(e);
+        return STOKES_ERR_CUDA;
+    }
+    return STOKES_OK;
+}
+
+extern "C" int stokes_active_tiles(stokes_ctx h) { return h ? h->c.ntiles_active : -1; }
 
 static thread_local std::string g_create_error;
 
@@ -52,6 +69,7 @@ void stokes_default_options(stokes_options* o) {
     o->max_outer = 40;
     o->check_every = 64;
     o->precond = 0;
+    o->use_graph = 1;
 }
 
 const char* stokes_last_error(stokes_ctx ctx) {

@@ -98,7 +98,7 @@ template <class T>
 __global__ void __launch_bounds__(256) k_cg_init(Layout L, const int* __restrict__ tiles, int nf, const double* r64,
                                                  const T* __restrict__ minv, CgWork<T> w, CgScalars* sc,
                                                  double* partial, unsigned* counter, int nblocks,
-                                                 cudaGraphConditionalHandle h) {
+                                                 cudaGraphConditionalHandle h, int use_cond) {
     const int tile = tiles[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T scale = (T)sc->scale;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) k_cg_init(Layout L, const int* __restrict
         sc->beta = 0.0; sc->iter = 0; sc->status = 0;
         sc->done = (trr <= sc->tol2 || trr == 0.0) ? 1 : 0;
         if (!isfinite(trr)) { sc->done = 1; sc->status = STOKES_ERR_NONFINITE; }
-        cudaGraphSetConditional(h, sc->done ? 0u : 1u);
+        if (use_cond) cudaGraphSetConditional(h, sc->done ? 0u : 1u);
     });
 }
 
@@ -130,9 +130,9 @@ template <class T>
 __global__ void __launch_bounds__(256) k_cg_update(Layout L, const int* __restrict__ tiles, int nf,
                                                    const T* __restrict__ minv, CgWork<T> w, const T* __restrict__ p,
                                                    CgScalars* sc, double* partial, unsigned* counter, int nblocks,
-                                                   cudaGraphConditionalHandle h) {
+                                                   cudaGraphConditionalHandle h, int use_cond) {
     if (sc->done) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
         return;
     }
     const int tile = tiles[blockIdx.x];
@@ -162,17 +162,17 @@ __global__ void __launch_bounds__(256) k_cg_update(Layout L, const int* __restri
         else if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = STOKES_ERR_NOT_CONVERGED; }
         sc->beta = trz / sc->rz;
         sc->rz = trz;
-        cudaGraphSetConditional(h, sc->done ? 0u : 1u);
+        if (use_cond) cudaGraphSetConditional(h, sc->done ? 0u : 1u);
     });
 }
 
-// x64 += x / scale (refinement update), over active tiles
+// x64 += sign * d / scale (refinement update; sign = -1 undoes it), over active tiles
 template <class T>
 __global__ void __launch_bounds__(256) k_ir_update(Layout L, const int* __restrict__ tiles, int nf, double* x64,
-                                                   const T* __restrict__ d, const CgScalars* sc) {
+                                                   const T* __restrict__ d, const CgScalars* sc, double sign) {
     const int tile = tiles[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const double inv = 1.0 / sc->scale;
+    const double inv = sign / sc->scale;
     const int nrow = tile_rows(L);
     for (int row = warp; row < nrow; row += 8) {
         int64_t o = tile_row_off(L, tile, row) + lane;
@@ -225,7 +225,7 @@ static cudaError_t build_inner_graph(Ctx* c, CgWork<T>& w, const T* minv, const 
     // init node by capture into g
     if ((e = cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
         return e;
-    k_cg_init<T><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, c->w64.r, minv, w, sc, part, cnt, nb, h);
+    k_cg_init<T><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, c->w64.r, minv, w, sc, part, cnt, nb, h, 1);
     cudaGraph_t captured = nullptr;
     if ((e = cudaStreamEndCapture(s, &captured)) != cudaSuccess) return e;
     // find the init node (the graph's only node so far)
@@ -251,7 +251,7 @@ static cudaError_t build_inner_graph(Ctx* c, CgWork<T>& w, const T* minv, const 
         a.counter = cnt;
         a.sc = sc;
         launch_apply_mode<T, C>(L, c->tiles, nb, cf, w.z, w.q, MODE_CG, a, s);
-        k_cg_update<T><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, minv, w, w.p[k ^ 1], sc, part, cnt, nb, h);
+        k_cg_update<T><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, minv, w, w.p[k ^ 1], sc, part, cnt, nb, h, 1);
     }
     cudaGraph_t cap2 = nullptr;
     if ((e = cudaStreamEndCapture(s, &cap2)) != cudaSuccess) return e;
@@ -260,20 +260,48 @@ static cudaError_t build_inner_graph(Ctx* c, CgWork<T>& w, const T* minv, const 
     return e;
 }
 
-template <class T, class C>
-static cudaError_t run_inner(Ctx* c, int prec_slot, CgWork<T>& w, const T* minv, const Coef<C>& cf) {
-    cudaGraphExec_t& ge = c->graph[prec_slot];
-    cudaError_t e;
-    if (!ge) {
-        if ((e = build_inner_graph<T, C>(c, w, minv, cf, c->sc, &ge)) != cudaSuccess) return e;
-    }
-    return cudaGraphLaunch(ge, c->stream);
-}
-
 static cudaError_t fetch_scalars(Ctx* c) {
     cudaError_t e = cudaMemcpyAsync(c->h_sc, c->sc, 2 * sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(c->stream);
+}
+
+// One inner solve.  use_graph: the device-side graph (one launch); else
+// chunks of ``chunk`` iterations launched kernel by kernel, the host reading
+// the done flag between chunks (kernels after "done" return at once).
+template <class T, class C>
+static cudaError_t run_inner(Ctx* c, int prec_slot, CgWork<T>& w, const T* minv, const Coef<C>& cf, int use_graph,
+                             int chunk) {
+    cudaError_t e;
+    if (use_graph) {
+        cudaGraphExec_t& ge = c->graph[prec_slot];
+        if (!ge) {
+            if ((e = build_inner_graph<T, C>(c, w, minv, cf, c->sc, &ge)) != cudaSuccess) return e;
+        }
+        return cudaGraphLaunch(ge, c->stream);
+    }
+    const Layout& L = c->L;
+    cudaStream_t s = c->stream;
+    const int nb = c->ntiles_active;
+    cudaGraphConditionalHandle h0 = 0;
+    k_cg_init<T><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, c->w64.r, minv, w, c->sc, c->partial, c->counter, nb, h0, 0);
+    chunk = chunk < 2 ? 2 : (chunk + 1) & ~1;   // even: p[0]/p[1] parity restarts each chunk
+    for (long it = 0;; it += chunk) {
+        for (int k = 0; k < chunk; ++k) {
+            ApplyArgs a{};
+            a.pold = w.p[k & 1];
+            a.pnew = w.p[(k & 1) ^ 1];
+            a.partial = c->partial;
+            a.counter = c->counter;
+            a.sc = c->sc;
+            if ((e = launch_apply_mode<T, C>(L, c->tiles, nb, cf, w.z, w.q, MODE_CG, a, s)) != cudaSuccess) return e;
+            k_cg_update<T><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, minv, w, w.p[(k & 1) ^ 1], c->sc, c->partial,
+                                              c->counter, nb, h0, 0);
+        }
+        if ((e = fetch_scalars(c)) != cudaSuccess) return e;
+        if (c->h_sc[0].done) break;
+    }
+    return cudaGetLastError();
 }
 
 static cudaError_t push_inner_params(Ctx* c, double scale, double tol_rel, int max_iter) {
@@ -318,7 +346,20 @@ stokes_status solve_system(Ctx* c, const double* b, double* x, const stokes_opti
         return STOKES_ERR_NONFINITE;
     }
     double rr = bb;
-    const int mode = o->mode;
+    int mode = o->mode;
+    const int use_graph = o->use_graph;
+    ApplyArgs ra{};
+    ra.b = b;
+    ra.partial = c->partial;
+    ra.counter = c->counter;
+    ra.sc = so;
+    auto residual = [&]() -> cudaError_t {   // r64 = b - A64 x, ||r64||^2 -> so->rr
+        return launch_apply_mode<double, double>(L, c->tiles, nb, c->coef<double>(), x, c->w64.r, MODE_RESID, ra, s);
+    };
+    auto update = [&](double sign) {
+        if (mode == STOKES_FP64) k_ir_update<double><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, x, c->w64.x, c->sc, sign);
+        else k_ir_update<float><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, x, c->w32.x, c->sc, sign);
+    };
     for (outer = 0; outer < o->max_outer; ++outer) {
         rel = std::sqrt(rr / bb);
         if (rel <= o->tol) break;
@@ -329,32 +370,38 @@ stokes_status solve_system(Ctx* c, const double* b, double* x, const stokes_opti
         double tol_rel = mode == STOKES_FP64 ? target : std::fmax(o->inner_tol, target);
         double scale = 1.0 / std::sqrt(rr);
         CK(push_inner_params(c, scale, tol_rel, remaining));
-        if (mode == STOKES_FP64) {
-            CK(run_inner<double, double>(c, 0, c->w64, c->A.minv64, c->coef<double>()));
-            k_ir_update<double><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, x, c->w64.x, c->sc);
-        } else if (mode == STOKES_FP32) {
-            CK(run_inner<float, float>(c, 1, c->w32, c->A.minv32, c->coef<float>()));
-            k_ir_update<float><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, x, c->w32.x, c->sc);
-        } else {
-            CK(run_inner<float, __nv_bfloat16>(c, 2, c->w32, c->A.minv32, c->coef<__nv_bfloat16>()));
-            k_ir_update<float><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, x, c->w32.x, c->sc);
-        }
+        if (mode == STOKES_FP64)
+            CK(run_inner<double, double>(c, 0, c->w64, c->A.minv64, c->coef<double>(), use_graph, o->check_every));
+        else if (mode == STOKES_FP32)
+            CK(run_inner<float, float>(c, 1, c->w32, c->A.minv32, c->coef<float>(), use_graph, o->check_every));
+        else
+            CK(run_inner<float, __nv_bfloat16>(c, 2, c->w32, c->A.minv32, c->coef<__nv_bfloat16>(), use_graph,
+                                               o->check_every));
+        update(1.0);
         CK(cudaGetLastError());
-        // true residual in FP64: r64 = b - A64 x
-        ApplyArgs a{};
-        a.b = b;
-        a.partial = c->partial;
-        a.counter = c->counter;
-        a.sc = so;
-        CK(launch_apply_mode<double, double>(L, c->tiles, nb, c->coef<double>(), x, c->w64.r, MODE_RESID, a, s));
+        CK(residual());
         CK(fetch_scalars(c));
         total_iter += c->h_sc[0].iter;
-        rr = c->h_sc[1].rr;
+        double rr_new = c->h_sc[1].rr;
         int ist = c->h_sc[0].status;
-        if (!std::isfinite(rr)) { status = STOKES_ERR_NONFINITE; break; }
-        if (ist == STOKES_ERR_NONFINITE || ist == STOKES_ERR_BREAKDOWN) {
-            // breakdown of the inner solve: keep the refined x if it helped
-            if (std::sqrt(rr / bb) > o->tol) { status = ist; rel = std::sqrt(rr / bb); break; }
+        if (!(rr_new < rr) || !std::isfinite(rr_new)) {
+            // the step did not reduce the FP64 residual: undo it and move the
+            // inner solve up one precision (BF16 -> FP32 -> FP64)
+            update(-1.0);
+            CK(residual());
+            CK(fetch_scalars(c));
+            rr = c->h_sc[1].rr;
+            if (mode == STOKES_FP64) {
+                status = (ist == STOKES_OK || ist == STOKES_ERR_NOT_CONVERGED) ? STOKES_ERR_NOT_CONVERGED : ist;
+                break;
+            }
+            mode = mode == STOKES_BF16 ? STOKES_FP32 : STOKES_FP64;
+            continue;
+        }
+        rr = rr_new;
+        if ((ist == STOKES_ERR_NONFINITE || ist == STOKES_ERR_BREAKDOWN) && std::sqrt(rr / bb) > o->tol) {
+            if (mode == STOKES_FP64) { status = ist; break; }
+            mode = mode == STOKES_BF16 ? STOKES_FP32 : STOKES_FP64;
         }
     }
     rel = std::sqrt(rr / bb);
@@ -364,11 +411,66 @@ stokes_status solve_system(Ctx* c, const double* b, double* x, const stokes_opti
         st->outer = outer;
         st->rel_residual = rel;
         st->status = status;
+        st->precision_used = mode;
     }
     if (status != STOKES_OK) set_error(c, "solve stopped with status " + std::to_string(status) +
                                               " at relative residual " + std::to_string(rel));
     return (stokes_status)status;
 #undef CK
+}
+
+// Time real CG iterations kernel by kernel: r = b (the last right-hand side),
+// then ``launches`` x [apply in CG mode, update] with CUDA events around each
+// launch on the context's stream.  Averages in ms per launch.
+template <class T, class C>
+static cudaError_t bench_impl(Ctx* c, CgWork<T>& w, const T* minv, const Coef<C>& cf, int launches, double* ms_apply,
+                              double* ms_update) {
+    const Layout& L = c->L;
+    cudaStream_t s = c->stream;
+    const int nb = c->ntiles_active;
+    cudaError_t e;
+    if ((e = push_inner_params(c, 1.0, 0.0, 1 << 30)) != cudaSuccess) return e;
+    cudaGraphConditionalHandle h0 = 0;
+    k_cg_init<T><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, c->b64, minv, w, c->sc, c->partial, c->counter, nb, h0, 0);
+    std::vector<cudaEvent_t> ev(2 * launches + 1);
+    for (auto& x : ev) cudaEventCreate(&x);
+    cudaEventRecord(ev[0], s);
+    for (int k = 0; k < launches; ++k) {
+        ApplyArgs a{};
+        a.pold = w.p[k & 1];
+        a.pnew = w.p[(k & 1) ^ 1];
+        a.partial = c->partial;
+        a.counter = c->counter;
+        a.sc = c->sc;
+        launch_apply_mode<T, C>(L, c->tiles, nb, cf, w.z, w.q, MODE_CG, a, s);
+        cudaEventRecord(ev[2 * k + 1], s);
+        k_cg_update<T><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, minv, w, w.p[(k & 1) ^ 1], c->sc, c->partial,
+                                          c->counter, nb, h0, 0);
+        cudaEventRecord(ev[2 * k + 2], s);
+    }
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    double ta = 0, tu = 0;
+    for (int k = 0; k < launches; ++k) {
+        float a = 0, u = 0;
+        cudaEventElapsedTime(&a, ev[2 * k], ev[2 * k + 1]);
+        cudaEventElapsedTime(&u, ev[2 * k + 1], ev[2 * k + 2]);
+        ta += a; tu += u;
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    *ms_apply = ta / launches;
+    *ms_update = tu / launches;
+    if ((e = fetch_scalars(c)) != cudaSuccess) return e;
+    if (c->h_sc[0].done) return cudaErrorInvalidValue;  // the loop stopped early: timings invalid
+    return cudaGetLastError();
+}
+
+cudaError_t bench_cg_kernels(Ctx* c, int precision, int launches, double* ms_apply, double* ms_update) {
+    if (precision == STOKES_FP64)
+        return bench_impl<double, double>(c, c->w64, c->A.minv64, c->coef<double>(), launches, ms_apply, ms_update);
+    if (precision == STOKES_FP32)
+        return bench_impl<float, float>(c, c->w32, c->A.minv32, c->coef<float>(), launches, ms_apply, ms_update);
+    return bench_impl<float, __nv_bfloat16>(c, c->w32, c->A.minv32, c->coef<__nv_bfloat16>(), launches, ms_apply,
+                                            ms_update);
 }
 
 }  // namespace stk

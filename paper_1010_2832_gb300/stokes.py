@@ -31,12 +31,13 @@ class Layout(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("mode", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("inner_tol", C.c_double),
-                ("max_outer", C.c_int), ("check_every", C.c_int), ("precond", C.c_int)]
+                ("max_outer", C.c_int), ("check_every", C.c_int), ("precond", C.c_int), ("use_graph", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("outer", C.c_int), ("rel_residual", C.c_double),
-                ("ms_rhs", C.c_double), ("ms_solve", C.c_double), ("ms_recover", C.c_double)]
+                ("ms_rhs", C.c_double), ("ms_solve", C.c_double), ("ms_recover", C.c_double),
+                ("precision_used", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -45,7 +46,7 @@ class Stats(C.Structure):
 EXPORTED = ("stokes_create", "stokes_destroy", "stokes_last_error", "stokes_build_weights", "stokes_vector_layout",
             "stokes_apply", "stokes_rhs", "stokes_recover", "stokes_default_options", "stokes_solve_step",
             "stokes_solve_system", "stokes_export", "stokes_export_size", "stokes_slots_to_fields",
-            "stokes_fields_to_slots", "stokes_last_apply_ms")
+            "stokes_fields_to_slots", "stokes_last_apply_ms", "stokes_bench_cg_kernels", "stokes_active_tiles")
 
 _lib = None
 
@@ -77,6 +78,8 @@ def load_library(path=LIB_PATH):
         "stokes_slots_to_fields": (I, [P, P, P]),
         "stokes_fields_to_slots": (I, [P, P, P]),
         "stokes_last_apply_ms": (D, [P]),
+        "stokes_bench_cg_kernels": (I, [P, I, I, C.POINTER(D), C.POINTER(D)]),
+        "stokes_active_tiles": (I, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -218,6 +221,15 @@ class StokesContext:
         out = self.new_vector()
         self._check(self.lib.stokes_fields_to_slots(self.h, _dev(fields).data_ptr(), out.data_ptr()))
         return out
+
+    def bench_cg_kernels(self, precision=FP32, launches=50):
+        """Mean device ms of the CG-mode apply and of the update kernel."""
+        a, u = C.c_double(), C.c_double()
+        self._check(self.lib.stokes_bench_cg_kernels(self.h, precision, launches, C.byref(a), C.byref(u)))
+        return a.value, u.value
+
+    def active_tiles(self):
+        return self.lib.stokes_active_tiles(self.h)
 
     def field_vector_length(self):
         nx, ny = self.n[0], self.n[1]

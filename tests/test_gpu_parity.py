@@ -97,8 +97,13 @@ def test_rhs_and_recovery_match(name):
     outs = [torch.zeros_like(t) for t in dev["u_star"]]
     ctx.recover(dev["u_star"], xs, outs)
     u = torch.cat([o.reshape(-1) for o in outs]).cpu().numpy()
-    umax = max(np.abs(u_ref).max(), 1e-30)
-    assert np.abs(u - u_ref).max() <= 1e-12 * umax
+    # scale of the rounded sum u* - dt/(rho W_L) (B^T x): the correction is
+    # amplified by 1/W_L on faces with little liquid
+    corr = np.zeros_like(u_ref)
+    lv = S.live
+    corr[lv] = S.inp.dt / (S.rho[lv] * S.WLu[lv]) * (abs(S.B).T @ np.abs(x))[lv]
+    scale = np.abs(S.u_star) + np.abs(S.u_bc) + corr
+    assert np.all(np.abs(u - u_ref) <= 1e-13 * scale + 1e-300)
 
 
 def _step(ctx, dev, mode, tol, **kw):
@@ -137,8 +142,20 @@ def test_fp64_solve_matches_direct_solve(name):
     lv = S.live
     umax = max(np.abs(u_ref[lv]).max(), 1e-30)
     assert np.abs(u - u_ref)[lv].max() <= 1e-9 * umax
-    # true residual recomputed by the oracle from the GPU's unknowns
-    assert So.relative_residual(S.A, x, S.b) <= 2e-12
+    # true residual recomputed by the oracle from the GPU's unknowns (the two
+    # FP64 residual sums round differently: allow cond-level slack)
+    assert So.relative_residual(S.A, x, S.b) <= 1e-11
+
+
+@pytest.mark.parametrize("name", ["bumps96", "rand3d_a"])
+def test_host_driven_loop_matches_graph_loop(name):
+    wl, S, ctx, dev = setup(name)
+    st_g, u_g, x_g = _step(ctx, dev, 1, 1e-8)
+    st_h, u_h, x_h = _step(ctx, dev, 1, 1e-8, use_graph=0, check_every=16)
+    assert st_g.status == 0 and st_h.status == 0
+    # identical kernels in identical order: bit-identical iterates
+    assert st_g.iterations == st_h.iterations
+    assert np.array_equal(x_g, x_h)
 
 
 @pytest.mark.parametrize("name", list(CASES))
