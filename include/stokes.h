@@ -239,6 +239,49 @@ double stokes_last_apply_ms(stokes_ctx ctx);
 stokes_status stokes_bench_cg_kernels(stokes_ctx ctx, int precision, int launches, double* ms_apply,
                                       double* ms_update);
 
+/*
+ * Batched solve of many independent 2D systems of uneven size (one context
+ * per instance, weights already built) in one persistent cooperative kernel
+ * replayed from a CUDA graph: right-hand sides, FP64 Jacobi-PCG of every
+ * instance with its own scalars and stopping test (true relative residual
+ * <= opt->tol, verified in FP64 before an instance retires), recovery and
+ * output unpacking.  All device waits inside the kernel are bounded; a wait
+ * that gives up returns STOKES_ERR_TIMEOUT.
+ *
+ * stokes_batch_create plans the batch (per-instance tile lists) and picks
+ * the tile height (4, 8 or 16 rows of 32 slots) and CTAs per SM by timing
+ * every candidate (an autotuner), caching the choice in a text file (path
+ * ``tune_cache``, else $STOKES_AUTOTUNE_CACHE, else
+ * $HOME/.cache/libstokes_autotune.txt) keyed by instance count, problem
+ * size class and GPU name.  The contexts must stay alive and unchanged
+ * (no new stokes_build_weights) for the life of the batch.
+ * stokes_batch_solve enqueues on the batch's own stream and synchronises;
+ * ``stats`` (n entries, may be NULL) receive per-instance results and
+ * ``ms`` (may be NULL) the device time of the whole batched step.
+ * The graph is re-captured when the io pointers change.
+ */
+typedef struct {
+    const double* u_star[3];   /* device, field layout (2D: u, v)          */
+    double* u_out[3];          /* device, field layout                     */
+    double* tau_out[5];        /* device, field layout (2D: tau_xx, tau_xy) */
+    double* p_out;             /* device, cells                             */
+} stokes_batch_io;
+
+typedef struct stokes_batch_s* stokes_batch;
+
+stokes_status stokes_batch_create(stokes_batch* out, int n, const stokes_ctx* ctxs, const stokes_options* opt,
+                                  const char* tune_cache);
+stokes_status stokes_batch_solve(stokes_batch b, const stokes_batch_io* io, stokes_stats* stats, double* ms);
+stokes_status stokes_batch_destroy(stokes_batch b);
+/* Tuning picked for the batch: tile rows, CTAs per SM, time per iteration
+ * (us) measured by the tuner, and whether the step runs from a captured
+ * graph (1) or from direct launches (0). */
+stokes_status stokes_batch_tuning(stokes_batch b, int* tile_rows, int* ctas_per_sm, double* us_per_iter,
+                                  int* graph_captured);
+/* One-shot convenience: create, solve once, destroy. */
+stokes_status stokes_solve_batched(int n, const stokes_ctx* ctxs, const stokes_batch_io* io,
+                                   const stokes_options* opt, stokes_stats* stats);
+
 /* Number of tiles holding an active unknown (2D tiles are 32 x 8 slots,
  * 3D tiles 32 x 4 x 4); every CG kernel launches one CTA per such tile. */
 int stokes_active_tiles(stokes_ctx ctx);

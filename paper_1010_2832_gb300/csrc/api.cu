@@ -9,9 +9,6 @@
 
 using namespace stk;
 
-struct stokes_ctx_s {
-    Ctx c;
-};
 
 namespace stk {
 void set_error(Ctx* c, const std::string& m) { c->err = m; }
@@ -108,7 +105,7 @@ stokes_status stokes_create(stokes_ctx* out, const stokes_grid* g, void* stream)
     L.dim = g->dim; L.nx = g->nx; L.ny = g->ny; L.nz = g->dim == 3 ? g->nz : 0;
     L.P = (int)round_up(g->nx + 3, TX);
     if (g->dim == 2) {
-        L.R = (int)round_up(g->ny + 3, TY2);
+        L.R = (int)round_up(g->ny + 3, 16);   // tile heights 4, 8 and 16 all divide R
         L.Q = 1;
         L.guard = round_up(L.P + 1, 32);
         L.ntx = L.P / TX; L.nty = L.R / TY2; L.ntz = 1;
@@ -137,6 +134,7 @@ stokes_status stokes_create(stokes_ctx* out, const stokes_grid* g, void* stream)
     size_t oC16 = add(sizeof(__nv_bfloat16) * S * c.ncoef);
     size_t oM64 = add(sizeof(double) * S * c.nf), oM32 = add(sizeof(float) * S * c.nf);
     size_t oTF = add(c.ntiles_all);
+    size_t oTF4 = add(g->dim == 2 ? (size_t)L.ntx * (L.R / 4) : 1);
     c.weight_bytes = wb;
     cudaError_t e = dalloc(c, &c.weight_block, wb);
     char* base = (char*)c.weight_block;
@@ -160,6 +158,7 @@ stokes_status stokes_create(stokes_ctx* out, const stokes_grid* g, void* stream)
         A.minv64 = (double*)(base + oM64);
         A.minv32 = (float*)(base + oM32);
         A.tile_flag = (uint8_t*)(base + oTF);
+        A.tile_flag4 = (uint8_t*)(base + oTF4);
     }
     const int64_t V = (int64_t)c.nf * S;
     if (e == cudaSuccess) e = dalloc(c, (void**)&c.tiles, sizeof(int) * c.ntiles_all);

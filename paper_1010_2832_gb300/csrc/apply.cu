@@ -17,41 +17,9 @@
 // the result is deterministic) which then updates the CG scalars.
 #include "internal.cuh"
 #include "ctx.cuh"
+#include "apply2d_tile.cuh"
 
 namespace stk {
-
-template <class T> struct Acc;
-template <> struct Acc<double> {
-    double s = 0.0;
-    __device__ void add(double a, double b) { s = fma(a, b, s); }
-    __device__ double warp() { return warp_sum(s); }
-};
-// FP32 vectors: products and sums kept as float-float pairs (TwoProd via FMA,
-// TwoSum) so the partial is accurate to ~2^-44 relative without FP64 math.
-template <> struct Acc<float> {
-    float hi = 0.f, lo = 0.f;
-    __device__ void add(float a, float b) {
-        float p = a * b;
-        float e = fmaf(a, b, -p);
-        float s, t;
-        two_sum(hi, p, s, t);
-        lo += t + e;
-        hi = s;
-    }
-    __device__ double warp() { return warp_sum_ff(hi, lo); }
-};
-
-template <class C> __device__ __forceinline__ float cvt(C v);
-template <> __device__ __forceinline__ float cvt<float>(float v) { return v; }
-template <> __device__ __forceinline__ float cvt<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-__device__ __forceinline__ double cvtd(double v) { return v; }
-
-template <class T, class C> __device__ __forceinline__ T ld(const C* p, int64_t o);
-template <> __device__ __forceinline__ double ld<double, double>(const double* p, int64_t o) { return __ldg(p + o); }
-template <> __device__ __forceinline__ float ld<float, float>(const float* p, int64_t o) { return __ldg(p + o); }
-template <> __device__ __forceinline__ float ld<float, __nv_bfloat16>(const __nv_bfloat16* p, int64_t o) {
-    return __bfloat162float(p[o]);
-}
 
 // Block reduction of one double per thread into partial[blockIdx.x], then the
 // last block sums all partials (index order) and calls fin(total).
@@ -87,83 +55,20 @@ __device__ void block_partial_and_finish(double v, double* partial, unsigned* co
     }
 }
 
-template <class T, int MODE>
-__device__ __forceinline__ T stage_val(const T* x, const T* pold, T beta, int64_t o) {
-    if (MODE == MODE_CG) return x[o] + beta * pold[o];
-    return x[o];
-}
-
 // ------------------------------- 2D -----------------------------------------
 template <class T, class C, int MODE>
 __global__ void __launch_bounds__(256) k_apply2d(Layout L, const int* __restrict__ tiles, Coef<C> cf,
                                                  const T* __restrict__ x, T* __restrict__ y, ApplyArgs args,
                                                  int nblocks) {
-    constexpr int TY = TY2;
-    __shared__ T sU[TY + 2][TX + 2], sV[TY + 2][TX + 2], sN[TY + 2][TX + 2];
-    __shared__ T sZu[TY + 1][TX + 1], sZv[TY + 1][TX + 1];
+    __shared__ Smem2<T, TY2> sm;
     if (MODE == MODE_CG && args.sc->done) return;
     const int tile = tiles ? tiles[blockIdx.x] : blockIdx.x;
-    const int c0 = (tile % L.ntx) * TX, r0 = (tile / L.ntx) * TY;
-    const int64_t S = L.stride;
-    const C *a_c = cf.f[0], *a_n = cf.f[1], *d_c = cf.f[2], *d_n = cf.f[3], *K_u = cf.f[4], *K_v = cf.f[5];
-    const T* pold = (const T*)args.pold;
-    T* pnew = (T*)args.pnew;
+    const int c0 = (tile % L.ntx) * TX, r0 = (tile / L.ntx) * TY2;
     T beta = MODE == MODE_CG ? (T)args.sc->beta : T(0);
-    const int t = threadIdx.x;
-    for (int e = t; e < (TY + 2) * (TX + 2); e += 256) {
-        int jj = e / (TX + 2), ii = e - jj * (TX + 2);
-        int64_t o = L.off(c0 - 1 + ii, r0 - 1 + jj, 0);
-        T ac = ld<T, C>(a_c, o), an = ld<T, C>(a_n, o);
-        T txx = stage_val<T, MODE>(x, pold, beta, o);
-        T txy = stage_val<T, MODE>(x + S, pold + S, beta, o);
-        T p = stage_val<T, MODE>(x + 2 * S, pold + 2 * S, beta, o);
-        if (MODE == MODE_CG && ii >= 1 && ii <= TX && jj >= 1 && jj <= TY) {
-            pnew[o] = txx; pnew[S + o] = txy; pnew[2 * S + o] = p;
-        }
-        sU[jj][ii] = ac * (p - txx);
-        sV[jj][ii] = ac * (p + txx);
-        sN[jj][ii] = an * txy;
-    }
-    __syncthreads();
-    for (int e = t; e < (TY + 1) * (TX + 1); e += 256) {
-        int jj = e / (TX + 1), ii = e - jj * (TX + 1);
-        T ku = ld<T, C>(K_u, L.off(c0 + ii, r0 - 1 + jj, 0));
-        T kv = ld<T, C>(K_v, L.off(c0 - 1 + ii, r0 + jj, 0));
-        sZu[jj][ii] = ku * ((sU[jj][ii + 1] - sU[jj][ii]) + (sN[jj][ii + 1] - sN[jj + 1][ii + 1]));
-        sZv[jj][ii] = kv * ((sV[jj + 1][ii] - sV[jj][ii]) + (sN[jj + 1][ii] - sN[jj + 1][ii + 1]));
-    }
-    __syncthreads();
-    const int tx = t & (TX - 1), ty = t / TX;
-    const int64_t o = L.off(c0 + tx, r0 + ty, 0);
-    T ac = ld<T, C>(a_c, o), an = ld<T, C>(a_n, o), dc = ld<T, C>(d_c, o), dn = ld<T, C>(d_n, o);
-    // own unknowns: the staged halo centre already holds them
-    T p_, txx, txy;
-    if (MODE == MODE_CG) {
-        txx = pnew[o]; txy = pnew[S + o]; p_ = pnew[2 * S + o];
-    } else {
-        txx = x[o]; txy = x[S + o]; p_ = x[2 * S + o];
-    }
-    T zu = sZu[ty + 1][tx], zur = sZu[ty + 1][tx + 1], zud = sZu[ty][tx];
-    T zv = sZv[ty][tx + 1], zvu = sZv[ty + 1][tx + 1], zvl = sZv[ty][tx];
-    T yp, yxx;
-    if (ac != T(0)) {
-        yp = ac * ((zu - zur) + (zv - zvu));
-        yxx = dc * txx + ac * ((zur - zu) + (zv - zvu));
-    } else {
-        yp = p_;
-        yxx = txx;
-    }
-    T yxy = dn * txy + an * ((zu - zud) + (zv - zvl));
-    if (MODE == MODE_RESID) {
-        const T* b = (const T*)args.b;
-        yxx = b[o] - yxx; yxy = b[S + o] - yxy; yp = b[2 * S + o] - yp;
-    }
-    y[o] = yxx; y[S + o] = yxy; y[2 * S + o] = yp;
+    double v = apply2d_tile<T, C, MODE, TY2, 256>(L, c0, r0, cf, x, y, (const T*)args.pold, (T*)args.pnew, beta,
+                                                    (const T*)args.b, sm);
     if (MODE != MODE_PLAIN) {
-        Acc<T> acc;
-        if (MODE == MODE_RESID) { acc.add(yxx, yxx); acc.add(yxy, yxy); acc.add(yp, yp); }
-        else { acc.add(txx, yxx); acc.add(txy, yxy); acc.add(p_, yp); }
-        double v = acc.warp();
+        const int t = threadIdx.x;
         if ((t & 31) != 0) v = 0.0;
         CgScalars* sc = args.sc;
         block_partial_and_finish<256>(v, args.partial, args.counter, nblocks, [&](double tot) {

@@ -1,0 +1,652 @@
+// Batched solve of many independent 2D systems (eq. stokesmixedsystemspd,
+// one per context) in one persistent cooperative kernel.
+//
+// Work list: the active tiles of every instance, concatenated (instance i
+// owns the contiguous range [tb_i, te_i)).  Each CTA walks the list with a
+// grid stride.  Per CG iteration, two phases separated by grid barriers:
+//   A  CG instances: p = z + beta p_old, q = A p, p.q   -> alpha
+//      CHECK instances: r = b - A x (true FP64 residual)
+//   B  CG instances: x += alpha p, r -= alpha q, z = M^-1 r, r.z, r.r
+//      CHECK instances: z = M^-1 r, r.z, r.r of the true residual
+// The CTA that reports an instance's last tile of a phase reduces that
+// instance's per-tile partials in list order (deterministic) and updates
+// its scalars: CG -> CHECK when the recurrence residual meets the
+// tolerance; CHECK -> done if the true residual meets it, else CG restarts
+// from the true residual.  Instances retire independently; the kernel ends
+// when all have.  Every grid barrier is a bounded wait: after ~2^24 polls
+// it records STOKES_ERR_TIMEOUT and every CTA returns.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+#include "internal.cuh"
+#include "ctx.cuh"
+#include "apply2d_tile.cuh"
+
+namespace stk {
+cudaError_t launch_rhs(Ctx* c, const double* const* ustar, double* b);
+cudaError_t launch_recover(Ctx* c, const double* const* ustar, const double* x, double* const* uout);
+cudaError_t launch_unpack(Ctx* c, const double* slots, double* const* fields, int to_fields);
+}  // namespace stk
+
+using namespace stk;
+
+namespace {
+
+struct BInst {
+    Layout L;
+    Coef<double> cf;
+    const double* minv;
+    const double* b;
+    double *x, *r, *z, *q;
+    double* p[2];
+    int tb, te;
+};
+
+struct BState {
+    double rz, rr, alpha, beta, tol2, bb;
+    int mode;      // 0 CG, 1 CHECK (true residual)
+    int parity, iter, done, status;
+    unsigned cnt;
+};
+
+struct BGlobal {
+    unsigned bar_count, bar_gen;
+    int ndone, err;
+};
+
+__device__ bool grid_sync(BGlobal* g, unsigned nblocks) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned* genp = &g->bar_gen;
+        volatile int* errp = &g->err;
+        unsigned gen = *genp;
+        __threadfence();
+        unsigned arrived = atomicAdd(&g->bar_count, 1u) + 1u;
+        if (arrived == nblocks) {
+            g->bar_count = 0u;
+            __threadfence();
+            atomicAdd(&g->bar_gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*genp == gen) {
+                if (*errp) { ok = 0; break; }
+                if (++spins > (1LL << 24)) { atomicExch(&g->err, (int)STOKES_ERR_TIMEOUT); ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok && !((volatile int*)&g->err)[0];
+}
+
+// Block-reduce two warp partials, store them for tile w, and let the CTA that
+// completes instance i's phase reduce all of i's tiles; fin(s0, s1) runs on
+// thread 0 of that CTA.
+template <class Fin>
+__device__ void tile_report(double v0, double v1, double* part, int w, BState* st, const BInst& I, Fin fin) {
+    __shared__ double red[2][8];
+    __shared__ bool last;
+    int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (lane == 0) { red[0][wp] = v0; red[1][wp] = v1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int q = 0; q < 8; ++q) { s0 += red[0][q]; s1 += red[1][q]; }
+        part[2 * w] = s0;
+        part[2 * w + 1] = s1;
+        __threadfence();
+        unsigned prev = atomicAdd(&st->cnt, 1u);
+        last = (prev == (unsigned)(I.te - I.tb) - 1u);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s0 = 0.0, s1 = 0.0;
+    for (int k = I.tb + threadIdx.x; k < I.te; k += 256) {
+        s0 += ((volatile double*)part)[2 * k];
+        s1 += ((volatile double*)part)[2 * k + 1];
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    __syncthreads();
+    if (lane == 0) { red[0][wp] = s0; red[1][wp] = s1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0;
+        for (int q = 0; q < 8; ++q) { t0 += red[0][q]; t1 += red[1][q]; }
+        fin(t0, t1);
+        st->cnt = 0u;
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+template <int TY>
+__global__ void __launch_bounds__(256) k_batched(const BInst* __restrict__ inst, BState* st,
+                                                 const int* __restrict__ wl_inst, const int* __restrict__ wl_c0,
+                                                 const int* __restrict__ wl_r0, int nwork, double* part, BGlobal* g,
+                                                 int ninst, int max_iter, double tol) {
+    __shared__ Smem2<double, TY> sm;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned nb = gridDim.x;
+    // ---- init: r = b, x = 0, z = M^-1 r, p = 0 ------------------------------
+    for (int w = blockIdx.x; w < nwork; w += nb) {
+        const int i = wl_inst[w];
+        const BInst& I = inst[i];
+        const int64_t S = I.L.stride;
+        double rz = 0.0, rr = 0.0;
+        for (int row = warp; row < TY; row += 8) {
+            int64_t o = I.L.off(wl_c0[w] + lane, wl_r0[w] + row, 0);
+            for (int f = 0; f < 3; ++f) {
+                int64_t of = f * S + o;
+                double r = I.b[of], z = I.minv[of] * r;
+                I.r[of] = r; I.z[of] = z; I.x[of] = 0.0; I.p[0][of] = 0.0; I.p[1][of] = 0.0;
+                rz = fma(r, z, rz); rr = fma(r, r, rr);
+            }
+        }
+        BState* s = st + i;
+        tile_report(warp_sum(rz), warp_sum(rr), part, w, s, I, [&](double trz, double trr) {
+            s->rz = trz; s->rr = trr; s->bb = trr; s->tol2 = tol * tol * trr;
+            s->mode = 0; s->parity = 0; s->iter = 0; s->beta = 0.0; s->status = 0;
+            s->done = trr == 0.0 ? 1 : 0;
+            if (!isfinite(trr)) { s->done = 1; s->status = STOKES_ERR_NONFINITE; }
+            if (s->done) atomicAdd(&g->ndone, 1);
+        });
+    }
+    if (!grid_sync(g, nb)) return;
+    for (;;) {
+        if (((volatile int*)&g->ndone)[0] >= ninst) return;
+        // ---- phase A ---------------------------------------------------------
+        for (int w = blockIdx.x; w < nwork; w += nb) {
+            const int i = wl_inst[w];
+            volatile BState* vs = st + i;
+            if (vs->done) continue;
+            const BInst& I = inst[i];
+            BState* s = st + i;
+            double v;
+            if (vs->mode == 0) {
+                int par = vs->parity;
+                v = apply2d_tile<double, double, MODE_CG, TY, 256>(I.L, wl_c0[w], wl_r0[w], I.cf, I.z, I.q,
+                                                                   I.p[par], I.p[par ^ 1], vs->beta, nullptr, sm);
+                tile_report(v, 0.0, part, w, s, I, [&](double pq, double) {
+                    if (!(pq > 0.0) || !isfinite(pq)) {
+                        s->done = 1;
+                        s->status = isfinite(pq) ? STOKES_ERR_BREAKDOWN : STOKES_ERR_NONFINITE;
+                        atomicAdd(&g->ndone, 1);
+                    } else {
+                        s->alpha = s->rz / pq;
+                    }
+                });
+            } else {
+                v = apply2d_tile<double, double, MODE_RESID, TY, 256>(I.L, wl_c0[w], wl_r0[w], I.cf, I.x, I.r,
+                                                                      nullptr, nullptr, 0.0, I.b, sm);
+                tile_report(v, 0.0, part, w, s, I, [&](double, double) {});
+            }
+            __syncthreads();
+        }
+        if (!grid_sync(g, nb)) return;
+        // ---- phase B ---------------------------------------------------------
+        for (int w = blockIdx.x; w < nwork; w += nb) {
+            const int i = wl_inst[w];
+            volatile BState* vs = st + i;
+            if (vs->done) continue;
+            const BInst& I = inst[i];
+            BState* s = st + i;
+            const int64_t S = I.L.stride;
+            const int mode = vs->mode;
+            const double alpha = vs->alpha;
+            const double* pn = I.p[vs->parity ^ 1];
+            double rz = 0.0, rr = 0.0;
+            for (int row = warp; row < TY; row += 8) {
+                int64_t o = I.L.off(wl_c0[w] + lane, wl_r0[w] + row, 0);
+                for (int f = 0; f < 3; ++f) {
+                    int64_t of = f * S + o;
+                    double r;
+                    if (mode == 0) {
+                        I.x[of] += alpha * pn[of];
+                        r = I.r[of] - alpha * I.q[of];
+                        I.r[of] = r;
+                    } else {
+                        r = I.r[of];
+                    }
+                    double z = I.minv[of] * r;
+                    I.z[of] = z;
+                    rz = fma(r, z, rz); rr = fma(r, r, rr);
+                }
+            }
+            tile_report(warp_sum(rz), warp_sum(rr), part, w, s, I, [&](double trz, double trr) {
+                s->rr = trr;
+                if (!isfinite(trr) || !isfinite(trz)) {
+                    s->done = 1; s->status = STOKES_ERR_NONFINITE; atomicAdd(&g->ndone, 1); return;
+                }
+                if (mode == 0) {
+                    s->iter += 1;
+                    if (trr <= s->tol2) {
+                        s->mode = 1;                       // verify with the true residual
+                    } else if (!(trz > 0.0)) {
+                        s->done = 1; s->status = STOKES_ERR_BREAKDOWN; atomicAdd(&g->ndone, 1);
+                    } else {
+                        s->beta = trz / s->rz; s->rz = trz; s->parity ^= 1;
+                    }
+                    if (!s->done && s->iter >= max_iter) {
+                        s->done = 1; s->status = STOKES_ERR_NOT_CONVERGED; atomicAdd(&g->ndone, 1);
+                    }
+                } else {
+                    if (trr <= s->tol2) {
+                        s->done = 1; atomicAdd(&g->ndone, 1);
+                    } else {                               // restart from the true residual
+                        s->mode = 0; s->beta = 0.0; s->rz = trz;
+                    }
+                }
+            });
+            __syncthreads();
+        }
+        if (!grid_sync(g, nb)) return;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side: plan (work lists per tile height), autotuner, graph.
+// ---------------------------------------------------------------------------
+struct stokes_batch_s {
+    std::vector<stokes_ctx> ctx;
+    std::vector<Ctx*> c;
+    int n = 0;
+    stokes_options opt{};
+    cudaStream_t s = nullptr;
+    int ty = 8, cps = 1;        // chosen tile height and CTAs per SM
+    double tuned_us = -1.0;
+    std::string err;
+    // device
+    BInst* d_inst = nullptr;
+    BState* d_st = nullptr;
+    BState* d_st0 = nullptr;    // initial states (empty instances already retired)
+    BGlobal* d_g0 = nullptr;
+    bool use_graph = true;
+    BGlobal* d_g = nullptr;
+    int* d_wl = nullptr;        // [3][nwork]
+    double* d_part = nullptr;
+    int nwork = 0;
+    int grid = 0;
+    std::vector<BState> h_st;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<const void*> io_key;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+static int num_sms() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+}
+
+template <int TY> static void* kernel_ptr() { return (void*)k_batched<TY>; }
+static void* kernel_for(int ty) {
+    return ty == 4 ? kernel_ptr<4>() : ty == 16 ? kernel_ptr<16>() : kernel_ptr<8>();
+}
+
+static int max_ctas_per_sm(int ty) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(ty), 256, 0);
+    return nb;
+}
+
+// active tiles of height ty (from the 32x4 activity flags of each context)
+static cudaError_t build_worklist(stokes_batch b, int ty, std::vector<int>& wi, std::vector<int>& wc,
+                                  std::vector<int>& wr, std::vector<BInst>& insts) {
+    wi.clear(); wc.clear(); wr.clear();
+    insts.resize(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        Ctx* c = b->c[i];
+        const Layout& L = c->L;
+        int n4 = L.R / 4;
+        std::vector<uint8_t> f4((size_t)L.ntx * n4);
+        cudaError_t e = cudaMemcpy(f4.data(), c->A.tile_flag4, f4.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return e;
+        BInst& I = insts[i];
+        I.L = L;
+        I.cf = c->coef<double>();
+        I.minv = c->A.minv64;
+        I.b = c->b64;
+        I.x = c->x64;
+        I.r = c->w64.r; I.z = c->w64.z; I.q = c->w64.q;
+        I.p[0] = c->w64.p[0]; I.p[1] = c->w64.p[1];
+        I.tb = (int)wi.size();
+        int per = ty / 4;
+        for (int tr = 0; tr < L.R / ty; ++tr)
+            for (int tx = 0; tx < L.ntx; ++tx) {
+                bool a = false;
+                for (int q = 0; q < per; ++q) a |= f4[(size_t)(tr * per + q) * L.ntx + tx] != 0;
+                if (a) { wi.push_back(i); wc.push_back(tx * TX); wr.push_back(tr * ty); }
+            }
+        I.te = (int)wi.size();
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t upload_plan(stokes_batch b, int ty) {
+    std::vector<int> wi, wc, wr;
+    std::vector<BInst> insts;
+    cudaError_t e = build_worklist(b, ty, wi, wc, wr, insts);
+    if (e != cudaSuccess) return e;
+    b->nwork = (int)wi.size();
+    std::vector<BState> st0(b->n);
+    std::memset(st0.data(), 0, st0.size() * sizeof(BState));
+    BGlobal g0{};
+    for (int i = 0; i < b->n; ++i)
+        if (insts[i].te == insts[i].tb) { st0[i].done = 1; g0.ndone += 1; }
+    if ((e = cudaMemcpy(b->d_st0, st0.data(), st0.size() * sizeof(BState), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpy(b->d_g0, &g0, sizeof(g0), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if (b->d_wl) { cudaFree(b->d_wl); b->d_wl = nullptr; }
+    if (b->d_part) { cudaFree(b->d_part); b->d_part = nullptr; }
+    size_t nw = std::max(1, b->nwork);
+    if ((e = cudaMalloc(&b->d_wl, 3 * nw * sizeof(int))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&b->d_part, 2 * nw * sizeof(double))) != cudaSuccess) return e;
+    if (b->nwork) {
+        cudaMemcpy(b->d_wl, wi.data(), wi.size() * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(b->d_wl + nw, wc.data(), wc.size() * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(b->d_wl + 2 * nw, wr.data(), wr.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
+    return cudaMemcpy(b->d_inst, insts.data(), insts.size() * sizeof(BInst), cudaMemcpyHostToDevice);
+}
+
+static cudaError_t launch_persistent(stokes_batch b, int ty, int grid, int max_iter, double tol) {
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(b->d_g, b->d_g0, sizeof(BGlobal), cudaMemcpyDeviceToDevice, b->s)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(b->d_st, b->d_st0, b->n * sizeof(BState), cudaMemcpyDeviceToDevice, b->s)) != cudaSuccess)
+        return e;
+    size_t nw = std::max(1, b->nwork);
+    const int* wi = b->d_wl;
+    const int* wc = b->d_wl + nw;
+    const int* wr = b->d_wl + 2 * nw;
+    void* args[] = {(void*)&b->d_inst, (void*)&b->d_st, (void*)&wi, (void*)&wc, (void*)&wr, (void*)&b->nwork,
+                    (void*)&b->d_part, (void*)&b->d_g, (void*)&b->n, (void*)&max_iter, (void*)&tol};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = b->s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, kernel_for(ty), args);
+}
+
+static std::string cache_path(const char* given) {
+    if (given && *given) return given;
+    const char* env = std::getenv("STOKES_AUTOTUNE_CACHE");
+    if (env && *env) return env;
+    const char* home = std::getenv("HOME");
+    return std::string(home ? home : ".") + "/.cache/libstokes_autotune.txt";
+}
+
+// Cache file: one line per key, "key ty cps us_per_iter".
+static bool cache_lookup(const std::string& path, const std::string& key, int& ty, int& cps, double& us) {
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line)) {
+        std::istringstream is(line);
+        std::string k;
+        int a, c;
+        double u;
+        if (is >> k >> a >> c >> u && k == key && (a == 4 || a == 8 || a == 16) && c >= 1) {
+            ty = a; cps = c; us = u;
+            return true;
+        }
+    }
+    return false;
+}
+
+static void cache_store(const std::string& path, const std::string& key, int ty, int cps, double us) {
+    std::vector<std::string> keep;
+    {
+        std::ifstream f(path);
+        std::string line;
+        while (std::getline(f, line))
+            if (line.compare(0, key.size() + 1, key + " ") != 0) keep.push_back(line);
+    }
+    std::string dir = path.substr(0, path.find_last_of('/'));
+    if (!dir.empty() && dir != path) { std::string cmd = "mkdir -p '" + dir + "' 2>/dev/null"; (void)!system(cmd.c_str()); }
+    std::ofstream f(path, std::ios::trunc);
+    for (auto& l : keep) f << l << "\n";
+    f << key << " " << ty << " " << cps << " " << us << "\n";
+}
+
+static std::string tune_key(stokes_batch b) {
+    long long slots = 0;
+    for (auto* c : b->c) slots += (long long)c->L.P * c->L.R;
+    int lg = 0;
+    while ((1LL << (lg + 1)) <= slots) ++lg;
+    cudaDeviceProp p{};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&p, dev);
+    std::string gpu = p.name;
+    for (auto& ch : gpu) if (ch == ' ') ch = '_';
+    return "batch2d_fp64_n" + std::to_string(b->n) + "_slots2^" + std::to_string(lg) + "_" + gpu;
+}
+
+static cudaError_t autotune(stokes_batch b, const char* cache) {
+    std::string path = cache_path(cache), key = tune_key(b);
+    int ty, cps;
+    double us;
+    if (cache_lookup(path, key, ty, cps, us) && cps <= max_ctas_per_sm(ty)) {
+        b->ty = ty; b->cps = cps; b->tuned_us = us;
+        return upload_plan(b, ty);
+    }
+    const int sms = num_sms();
+    const int iters = 24;
+    double best = 1e30;
+    int bt = 8, bc = 1;
+    for (int t : {4, 8, 16}) {
+        cudaError_t e = upload_plan(b, t);
+        if (e != cudaSuccess) return e;
+        int mx = max_ctas_per_sm(t);
+        for (int c = 1; c <= std::min(mx, 4); ++c) {
+            int grid = std::min(sms * c, std::max(1, b->nwork));
+            // warm run, then a timed run of a fixed number of iterations
+            if ((e = launch_persistent(b, t, grid, 4, 0.0)) != cudaSuccess) return e;
+            cudaEventRecord(b->ev0, b->s);
+            if ((e = launch_persistent(b, t, grid, iters, 0.0)) != cudaSuccess) return e;
+            cudaEventRecord(b->ev1, b->s);
+            if ((e = cudaEventSynchronize(b->ev1)) != cudaSuccess) return e;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+            double per = 1000.0 * ms / iters;
+            if (per < best) { best = per; bt = t; bc = c; }
+        }
+    }
+    b->ty = bt; b->cps = bc; b->tuned_us = best;
+    cache_store(path, key, bt, bc, best);
+    return upload_plan(b, bt);
+}
+
+// right-hand sides, the persistent solve, recovery and unpacking, on b->s
+static cudaError_t enqueue(stokes_batch b, const stokes_batch_io* io) {
+    for (int i = 0; i < b->n; ++i) {
+        Ctx* c = b->c[i];
+        cudaStream_t keep = c->stream;
+        c->stream = b->s;
+        launch_rhs(c, io[i].u_star, c->b64);
+        c->stream = keep;
+    }
+    launch_persistent(b, b->ty, b->grid, b->opt.max_iter, b->opt.tol);
+    for (int i = 0; i < b->n; ++i) {
+        Ctx* c = b->c[i];
+        cudaStream_t keep = c->stream;
+        c->stream = b->s;
+        launch_recover(c, io[i].u_star, c->x64, io[i].u_out);
+        double* outs[6];
+        for (int f = 0; f < c->nf - 1; ++f) outs[f] = io[i].tau_out[f];
+        outs[c->nf - 1] = io[i].p_out;
+        launch_unpack(c, c->x64, outs, 1);
+        c->stream = keep;
+    }
+    return cudaGetLastError();
+}
+
+// Capture enqueue() into a CUDA graph; if the cooperative launch cannot be
+// captured, fall back to enqueueing directly on every solve.
+static cudaError_t capture(stokes_batch b, const stokes_batch_io* io) {
+    cudaError_t e;
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    const int sms = num_sms();
+    b->grid = std::min(sms * b->cps, std::max(1, b->nwork));
+    if ((e = cudaStreamBeginCapture(b->s, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return e;
+    cudaError_t ee = enqueue(b, io);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->s, &g);
+    if (ee == cudaSuccess && e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (ee != cudaSuccess || e != cudaSuccess) {
+        cudaGetLastError();
+        b->use_graph = false;
+        b->graph = nullptr;
+    }
+    return cudaSuccess;
+}
+
+static std::vector<const void*> io_pointers(const stokes_batch_io* io, int n) {
+    std::vector<const void*> v;
+    for (int i = 0; i < n; ++i) {
+        for (int d = 0; d < 2; ++d) { v.push_back(io[i].u_star[d]); v.push_back(io[i].u_out[d]); }
+        for (int f = 0; f < 2; ++f) v.push_back(io[i].tau_out[f]);
+        v.push_back(io[i].p_out);
+    }
+    return v;
+}
+
+extern "C" {
+
+stokes_status stokes_batch_destroy(stokes_batch b) {
+    if (!b) return STOKES_OK;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->d_inst); cudaFree(b->d_st); cudaFree(b->d_g); cudaFree(b->d_wl); cudaFree(b->d_part);
+    cudaFree(b->d_st0); cudaFree(b->d_g0);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    if (b->s) cudaStreamDestroy(b->s);
+    delete b;
+    return STOKES_OK;
+}
+
+stokes_status stokes_batch_create(stokes_batch* out, int n, const stokes_ctx* ctxs, const stokes_options* opt,
+                                  const char* tune_cache) {
+    if (!out || n < 1 || !ctxs || !opt) return STOKES_ERR_ARG;
+    *out = nullptr;
+    auto* b = new stokes_batch_s();
+    b->n = n;
+    b->opt = *opt;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || ctxs[i]->c.L.dim != 2 || !ctxs[i]->c.have_weights) {
+            delete b;
+            return STOKES_ERR_ARG;
+        }
+        b->ctx.push_back(ctxs[i]);
+        b->c.push_back(&ctxs[i]->c);
+        cudaStreamSynchronize(ctxs[i]->c.stream);
+    }
+    cudaError_t e = cudaStreamCreate(&b->s);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_inst, n * sizeof(BInst));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_st, n * sizeof(BState));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_g, sizeof(BGlobal));
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    // each context's right-hand side must hold something finite for tuning
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        e = cudaMemsetAsync(b->c[i]->b64, 0, sizeof(double) * b->c[i]->vec_elems(), b->s);
+    if (e == cudaSuccess) e = autotune(b, tune_cache);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+    if (e != cudaSuccess) {
+        stokes_batch_destroy(b);
+        return STOKES_ERR_CUDA;
+    }
+    b->h_st.resize(n);
+    *out = b;
+    return STOKES_OK;
+}
+
+stokes_status stokes_batch_tuning(stokes_batch b, int* tile_rows, int* ctas_per_sm, double* us_per_iter,
+                                  int* graph_captured) {
+    if (!b) return STOKES_ERR_ARG;
+    if (graph_captured) *graph_captured = b->use_graph && b->graph ? 1 : 0;
+    if (tile_rows) *tile_rows = b->ty;
+    if (ctas_per_sm) *ctas_per_sm = b->cps;
+    if (us_per_iter) *us_per_iter = b->tuned_us;
+    return STOKES_OK;
+}
+
+stokes_status stokes_batch_solve(stokes_batch b, const stokes_batch_io* io, stokes_stats* stats, double* ms) {
+    if (!b || !io) return STOKES_ERR_ARG;
+    for (int i = 0; i < b->n; ++i) {
+        if (!io[i].u_star[0] || !io[i].u_star[1] || !io[i].u_out[0] || !io[i].u_out[1] || !io[i].tau_out[0] ||
+            !io[i].tau_out[1] || !io[i].p_out)
+            return STOKES_ERR_ARG;
+        cudaStreamSynchronize(b->c[i]->stream);
+    }
+    cudaError_t e = cudaSuccess;
+    auto key = io_pointers(io, b->n);
+    if (b->use_graph && (!b->graph || key != b->io_key)) {
+        e = capture(b, io);
+        if (e != cudaSuccess) return STOKES_ERR_CUDA;
+        b->io_key = key;
+    }
+    if (!b->use_graph) b->grid = std::min(num_sms() * b->cps, std::max(1, b->nwork));
+    cudaEventRecord(b->ev0, b->s);
+    e = b->use_graph ? cudaGraphLaunch(b->graph, b->s) : enqueue(b, io);
+    cudaEventRecord(b->ev1, b->s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b->ev1);
+    if (e != cudaSuccess) return STOKES_ERR_CUDA;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, b->ev0, b->ev1);
+    if (ms) *ms = t;
+    BGlobal g{};
+    cudaMemcpy(&g, b->d_g, sizeof(g), cudaMemcpyDeviceToHost);
+    cudaMemcpy(b->h_st.data(), b->d_st, b->n * sizeof(BState), cudaMemcpyDeviceToHost);
+    int worst = STOKES_OK;
+    for (int i = 0; i < b->n; ++i) {
+        const BState& s = b->h_st[i];
+        if (stats) {
+            stokes_stats& o = stats[i];
+            std::memset(&o, 0, sizeof(o));
+            o.status = g.err ? g.err : s.status;
+            o.iterations = s.iter;
+            o.outer = 1;
+            o.rel_residual = s.bb > 0 ? std::sqrt(s.rr / s.bb) : 0.0;
+            o.ms_solve = t;
+            o.precision_used = STOKES_FP64;
+        }
+        if (s.status != STOKES_OK && worst == STOKES_OK) worst = s.status;
+    }
+    if (g.err) return (stokes_status)g.err;
+    return (stokes_status)worst;
+}
+
+stokes_status stokes_solve_batched(int n, const stokes_ctx* ctxs, const stokes_batch_io* io, const stokes_options* opt,
+                                   stokes_stats* stats) {
+    stokes_batch b = nullptr;
+    stokes_status s = stokes_batch_create(&b, n, ctxs, opt, nullptr);
+    if (s != STOKES_OK) return s;
+    s = stokes_batch_solve(b, io, stats, nullptr);
+    stokes_batch_destroy(b);
+    return s;
+}
+
+}  // extern "C"

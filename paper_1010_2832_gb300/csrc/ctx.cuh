@@ -25,6 +25,7 @@ struct DevArrays {
     double* minv64;
     float* minv32;
     uint8_t* tile_flag;
+    uint8_t* tile_flag4;  // 2D: activity of 32 x 4 tiles (batched solver plans)
 };
 
 // Work vectors of one precision.
@@ -94,3 +95,7 @@ cudaError_t launch_apply_mode(const Layout& L, const int* tiles, int ntiles, con
                               int mode, const ApplyArgs& a, cudaStream_t s);
 
 }  // namespace stk
+
+struct stokes_ctx_s {
+    stk::Ctx c;
+};

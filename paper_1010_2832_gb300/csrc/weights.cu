@@ -425,6 +425,7 @@ __global__ void k_finish2d(Layout L, DevArrays D) {
     if (tile_act) {
         int c = i + 1, r = j + 1;
         D.tile_flag[(r / TY2) * L.ntx + c / TX] = 1;
+        D.tile_flag4[(r / 4) * L.ntx + c / TX] = 1;
     }
 }
 

@@ -46,7 +46,14 @@ class Stats(C.Structure):
 EXPORTED = ("stokes_create", "stokes_destroy", "stokes_last_error", "stokes_build_weights", "stokes_vector_layout",
             "stokes_apply", "stokes_rhs", "stokes_recover", "stokes_default_options", "stokes_solve_step",
             "stokes_solve_system", "stokes_export", "stokes_export_size", "stokes_slots_to_fields",
-            "stokes_fields_to_slots", "stokes_last_apply_ms", "stokes_bench_cg_kernels", "stokes_active_tiles")
+            "stokes_fields_to_slots", "stokes_last_apply_ms", "stokes_bench_cg_kernels", "stokes_active_tiles",
+            "stokes_batch_create", "stokes_batch_solve", "stokes_batch_destroy", "stokes_batch_tuning",
+            "stokes_solve_batched")
+
+
+class BatchIO(C.Structure):
+    _fields_ = [("u_star", C.c_void_p * 3), ("u_out", C.c_void_p * 3), ("tau_out", C.c_void_p * 5),
+                ("p_out", C.c_void_p)]
 
 _lib = None
 
@@ -80,6 +87,11 @@ def load_library(path=LIB_PATH):
         "stokes_last_apply_ms": (D, [P]),
         "stokes_bench_cg_kernels": (I, [P, I, I, C.POINTER(D), C.POINTER(D)]),
         "stokes_active_tiles": (I, [P]),
+        "stokes_batch_create": (I, [C.POINTER(P), I, C.POINTER(P), C.POINTER(Options), C.c_char_p]),
+        "stokes_batch_solve": (I, [P, C.POINTER(BatchIO), C.POINTER(Stats), C.POINTER(D)]),
+        "stokes_batch_destroy": (I, [P]),
+        "stokes_batch_tuning": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(D), C.POINTER(I)]),
+        "stokes_solve_batched": (I, [I, C.POINTER(P), C.POINTER(BatchIO), C.POINTER(Options), C.POINTER(Stats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -238,6 +250,57 @@ class StokesContext:
         nz = self.n[2]
         return (3 * nx * ny * nz + nz * (ny + 1) * (nx + 1) + (nz + 1) * ny * (nx + 1)
                 + (nz + 1) * (ny + 1) * nx)
+
+
+class Batch:
+    """Many 2D contexts solved together in one persistent launch (see
+    stokes_batch_create in include/stokes.h)."""
+
+    def __init__(self, contexts, options=None, tune_cache=None):
+        self.lib = load_library()
+        self.contexts = list(contexts)
+        n = len(self.contexts)
+        arr = (C.c_void_p * n)(*[c.h.value for c in self.contexts])
+        self.opt = options or default_options()
+        h = C.c_void_p()
+        st = self.lib.stokes_batch_create(C.byref(h), n, arr, C.byref(self.opt),
+                                          tune_cache.encode() if tune_cache else None)
+        if st != 0:
+            raise StokesError(st, "stokes_batch_create failed")
+        self.h = h
+
+    def tuning(self):
+        ty, cps, us, g = C.c_int(), C.c_int(), C.c_double(), C.c_int()
+        self.lib.stokes_batch_tuning(self.h, C.byref(ty), C.byref(cps), C.byref(us), C.byref(g))
+        return dict(tile_rows=ty.value, ctas_per_sm=cps.value, us_per_iter=us.value, graph=bool(g.value))
+
+    def solve(self, u_star, u_out, tau_out, p_out):
+        """Lists (one entry per instance) of tensors in field layout."""
+        n = len(self.contexts)
+        io = (BatchIO * n)()
+        for i in range(n):
+            for d in range(2):
+                io[i].u_star[d] = _dev(u_star[i][d]).data_ptr()
+                io[i].u_out[d] = _dev(u_out[i][d]).data_ptr()
+                io[i].tau_out[d] = _dev(tau_out[i][d]).data_ptr()
+            io[i].p_out = _dev(p_out[i]).data_ptr()
+        stats = (Stats * n)()
+        ms = C.c_double()
+        rc = self.lib.stokes_batch_solve(self.h, io, stats, C.byref(ms))
+        if rc not in (0, -3):
+            raise StokesError(rc, "stokes_batch_solve failed")
+        return [s.as_dict() for s in stats], ms.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.stokes_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def upload_workload(wl):

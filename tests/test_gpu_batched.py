@@ -1,0 +1,92 @@
+"""Batched persistent solve of uneven 2D instances vs single solves and the
+oracle.  Each instance's velocities must match the oracle's direct solve as
+closely as a single FP64 solve does (1e-9 relative at tol 1e-12), and every
+instance must retire at the requested true residual."""
+import numpy as np
+import pytest
+
+from gpu_common import gpu_context, oracle_system, require_gpu
+from oracle import solve as So
+from oracle import system as S_
+from paper_1010_2832_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _outputs(wl):
+    nx, ny = wl.n
+    u = [torch.zeros(a.shape, dtype=torch.float64, device="cuda") for a in wl.u_star]
+    t = [torch.zeros(nx * ny, dtype=torch.float64, device="cuda"),
+         torch.zeros((nx + 1) * (ny + 1), dtype=torch.float64, device="cuda")]
+    p = torch.zeros(nx * ny, dtype=torch.float64, device="cuda")
+    return u, t, p
+
+
+def _batch(wls, tol, tmp_path):
+    from paper_1010_2832_gb300 import stokes
+    ctxs, devs = zip(*[gpu_context(wl) for wl in wls])
+    opt = stokes.default_options(mode=0, tol=tol)
+    b = stokes.Batch(ctxs, opt, tune_cache=str(tmp_path / "tune.txt"))
+    outs = [_outputs(wl) for wl in wls]
+    stats, ms = b.solve([d["u_star"] for d in devs], [o[0] for o in outs], [o[1] for o in outs],
+                        [o[2] for o in outs])
+    return b, ctxs, devs, outs, stats, ms
+
+
+def test_batched_matches_oracle_on_uneven_instances(tmp_path):
+    require_gpu()
+    wls = [W.bumps_2d(n, seed=40 + i, rho_split=False, disk_r=0.05 + 0.02 * i) for i, n in
+           enumerate([24, 40, 33, 64, 17])]
+    wls.append(W.disk_in_box(16, radius=-1.0))   # an instance without liquid
+    b, ctxs, devs, outs, stats, ms = _batch(wls, 1e-12, tmp_path)
+    tun = b.tuning()
+    assert tun["tile_rows"] in (4, 8, 16) and tun["ctas_per_sm"] >= 1
+    for wl, st, (u, t, p) in zip(wls, stats, outs):
+        assert st["status"] == 0, st
+        S = oracle_system(wl)
+        if not S.active.any():
+            assert st["iterations"] == 0
+            continue
+        assert st["rel_residual"] <= 1e-12
+        x = torch.cat(t + [p]).cpu().numpy()
+        assert So.relative_residual(S.A, x, S.b) <= 1e-11
+        x_ref = So.solve_direct(S.A, S.b, S_.pressure_null_vectors(S))
+        u_ref = S_.recover_velocity(S, x_ref)
+        ug = torch.cat([a.reshape(-1) for a in u]).cpu().numpy()
+        lv = S.live
+        assert np.abs(ug - u_ref)[lv].max() <= 1e-9 * np.abs(u_ref[lv]).max()
+
+
+def test_batched_replay_and_tuning_cache(tmp_path):
+    require_gpu()
+    wls = [W.bumps_2d(n, seed=70 + n, rho_split=False) for n in (32, 48)]
+    b, ctxs, devs, outs, stats, ms = _batch(wls, 1e-8, tmp_path)
+    first = [torch.cat([a.reshape(-1) for a in o[0]]).cpu().numpy() for o in outs]
+    # replay the captured step: identical results (deterministic reductions)
+    stats2, ms2 = b.solve([d["u_star"] for d in devs], [o[0] for o in outs], [o[1] for o in outs],
+                          [o[2] for o in outs])
+    again = [torch.cat([a.reshape(-1) for a in o[0]]).cpu().numpy() for o in outs]
+    for a, c in zip(first, again):
+        assert np.array_equal(a, c)
+    assert [s["iterations"] for s in stats] == [s["iterations"] for s in stats2]
+    text = (tmp_path / "tune.txt").read_text()
+    assert text.strip().startswith("batch2d_fp64_n2_")
+    # a second batch reads the cached choice instead of re-timing
+    from paper_1010_2832_gb300 import stokes
+    b2 = stokes.Batch(ctxs, stokes.default_options(mode=0, tol=1e-8), tune_cache=str(tmp_path / "tune.txt"))
+    assert b2.tuning()["tile_rows"] == b.tuning()["tile_rows"]
+
+
+def test_batched_agrees_with_single_solves(tmp_path):
+    require_gpu()
+    from paper_1010_2832_gb300 import stokes
+    wls = W.batch_instances(count=4, n_lo=40, n_hi=90, seed0=4100)
+    b, ctxs, devs, outs, stats, ms = _batch(wls, 1e-8, tmp_path)
+    for wl, ctx, d, st, (u, t, p) in zip(wls, ctxs, devs, stats, outs):
+        u1, t1, p1 = _outputs(wl)
+        s1 = ctx.solve_step(d["u_star"], u1, t1, p1, stokes.default_options(mode=0, tol=1e-8))
+        assert st["status"] == 0 and s1.status == 0
+        a = torch.cat([x.reshape(-1) for x in u]).cpu().numpy()
+        c = torch.cat([x.reshape(-1) for x in u1]).cpu().numpy()
+        assert np.abs(a - c).max() <= 1e-5 * max(np.abs(c).max(), 1e-30)
