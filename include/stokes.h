@@ -282,6 +282,61 @@ stokes_status stokes_batch_tuning(stokes_batch b, int* tile_rows, int* ctas_per_
 stokes_status stokes_solve_batched(int n, const stokes_ctx* ctxs, const stokes_batch_io* io,
                                    const stokes_options* opt, stokes_stats* stats);
 
+/*
+ * Learned preconditioner network (not in the paper: a data-driven
+ * preconditioner for the CG solve).  A three-level U-Net on the slot lattice
+ * (convolutions 3x3 in 2D, 3x3x3 in 3D, widths 8/16/32, ReLU, 2x average
+ * pooling, nearest upsampling, skip concatenation, 1x1 output).  Activations
+ * are BF16, accumulation and master weights FP32.  Tensors passed in are FP32
+ * device arrays, channel-last (B, D, H, W, C) with D = 1 in 2D, H and W
+ * multiples of 4 (D too in 3D); ``cin`` and ``cout`` must be one of 4, 8,
+ * 12, 16, 24, 32, 48.  The flat parameter vector holds, per convolution in
+ * the order enc0a enc0b enc1a enc1b enc2a enc2b dec1a dec1b dec0a dec0b out,
+ * the weights W[tap][cin][cout] then the bias (stokes_net_layer gives the
+ * offsets).  All calls run on the network's own stream and synchronise.
+ */
+typedef struct stokes_net_s* stokes_net;
+
+stokes_status stokes_net_create(stokes_net* out, int dim, int cin, int cout, int64_t max_voxels);
+stokes_status stokes_net_destroy(stokes_net net);
+int64_t stokes_net_param_count(stokes_net net);
+stokes_status stokes_net_layer(stokes_net net, int i, int* cin, int* cout, int* ksize, int64_t* w_off,
+                               int64_t* b_off);
+stokes_status stokes_net_set_params(stokes_net net, const float* host_params);
+stokes_status stokes_net_get_params(stokes_net net, float* host_params);
+stokes_status stokes_net_forward(stokes_net net, int B, int D, int H, int W, const float* x, float* y);
+/* loss = mean over the batch of ||N(x_b) - y_b||^2 / ||y_b||^2, and its
+ * gradient with respect to the parameters (copied to grad_host if given). */
+stokes_status stokes_net_gradient(stokes_net net, int B, int D, int H, int W, const float* x, const float* y,
+                                  double* loss, float* grad_host);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on that loss. */
+stokes_status stokes_net_train_step(stokes_net net, int B, int D, int H, int W, const float* x, const float* y,
+                                    float lr, double* loss);
+
+/*
+ * Learned preconditioner for a context.  The network sees, per slot (i, j[, k])
+ * at voxel (k, j, i) of a grid padded to multiples of 4 (stokes_learned_grid),
+ * the Jacobi-scaled residual sqrt(m_f) r_f normalised to unit RMS over the
+ * active unknowns, and log(m_f)/16 (m = inverse diagonal of A), one channel
+ * per unknown field each, zero-padded to cin = 8 (2D) or 12 (3D); its output
+ * channels (cout = 4 or 8) give the preconditioned residual
+ * z_f = sqrt(m_f) out_f rms on active unknowns.  With options.precond = 1
+ * (mode FP32 or BF16) the inner solve is flexible CG (Polak-Ribiere beta)
+ * with this preconditioner, falling back to the Jacobi direction for a step
+ * whose network direction fails r.z > 0, inside the same FP64 refinement
+ * loop.  Re-attach after every stokes_build_weights.
+ */
+stokes_status stokes_set_learned_preconditioner(stokes_ctx ctx, stokes_net net);
+stokes_status stokes_learned_grid(stokes_ctx ctx, int* D, int* H, int* W, int* cin, int* cout);
+/* Network input for an FP64 slot-layout residual r (device) into x (device,
+ * FP32, D*H*W*cin); *rms receives the normalisation used. */
+stokes_status stokes_learned_features(stokes_ctx ctx, const double* r, float* x, double* rms);
+/* Training target for an FP64 slot-layout error e with the rms of its
+ * residual: y_f = e_f / (sqrt(m_f) rms) on active unknowns, 0 elsewhere. */
+stokes_status stokes_learned_targets(stokes_ctx ctx, const double* e, double rms, float* y);
+/* Steps at which the flexible CG fell back to the Jacobi direction. */
+long stokes_learned_jacobi_steps(stokes_ctx ctx);
+
 /* Number of tiles holding an active unknown (2D tiles are 32 x 8 slots,
  * 3D tiles 32 x 4 x 4); every CG kernel launches one CTA per such tile. */
 int stokes_active_tiles(stokes_ctx ctx);

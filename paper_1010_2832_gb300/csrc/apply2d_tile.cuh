@@ -42,6 +42,7 @@ __device__ __forceinline__ T stage_val(const T* x, const T* pold, T beta, int64_
 template <class T, int TY> struct Smem2 {
     T U[TY + 2][TX + 2], V[TY + 2][TX + 2], N[TY + 2][TX + 2];
     T Zu[TY + 1][TX + 1], Zv[TY + 1][TX + 1];
+    T own[3][TY][TX];   // the tile's own unknowns (after the direction update)
 };
 
 // Apply on the tile whose lower corner is (c0, r0) in padded coordinates.
@@ -55,6 +56,31 @@ __device__ double apply2d_tile(const Layout& L, int c0, int r0, const Coef<C>& c
     const int64_t S = L.stride;
     const C *a_c = cf.f[0], *a_n = cf.f[1], *d_c = cf.f[2], *d_n = cf.f[3], *K_u = cf.f[4], *K_v = cf.f[5];
     const int t = threadIdx.x;
+    // Every global load of the tile is issued up front (face coefficients and
+    // the own slots' coefficients into registers), so one CTA waits for one
+    // memory round trip rather than three.
+    constexpr int NFACE = ((TY + 1) * (TX + 1) + NT - 1) / NT;
+    constexpr int NOWN = (TY * TX + NT - 1) / NT;
+    T ku[NFACE], kv[NFACE];
+#pragma unroll
+    for (int q = 0; q < NFACE; ++q) {
+        int e = t + q * NT;
+        if (e < (TY + 1) * (TX + 1)) {
+            int jj = e / (TX + 1), ii = e - jj * (TX + 1);
+            ku[q] = ld<T, C>(K_u, L.off(c0 + ii, r0 - 1 + jj, 0));
+            kv[q] = ld<T, C>(K_v, L.off(c0 - 1 + ii, r0 + jj, 0));
+        }
+    }
+    T oac[NOWN], oan[NOWN], odc[NOWN], odn[NOWN];
+#pragma unroll
+    for (int q = 0; q < NOWN; ++q) {
+        int e = t + q * NT;
+        if (e < TY * TX) {
+            const int64_t o = L.off(c0 + (e & (TX - 1)), r0 + e / TX, 0);
+            oac[q] = ld<T, C>(a_c, o); oan[q] = ld<T, C>(a_n, o);
+            odc[q] = ld<T, C>(d_c, o); odn[q] = ld<T, C>(d_n, o);
+        }
+    }
     for (int e = t; e < (TY + 2) * (TX + 2); e += NT) {
         int jj = e / (TX + 2), ii = e - jj * (TX + 2);
         int64_t o = L.off(c0 - 1 + ii, r0 - 1 + jj, 0);
@@ -62,33 +88,36 @@ __device__ double apply2d_tile(const Layout& L, int c0, int r0, const Coef<C>& c
         T txx = stage_val<T, MODE>(x, pold, beta, o);
         T txy = stage_val<T, MODE>(x + S, pold + S, beta, o);
         T p = stage_val<T, MODE>(x + 2 * S, pold + 2 * S, beta, o);
-        if (MODE == MODE_CG && ii >= 1 && ii <= TX && jj >= 1 && jj <= TY) {
-            pnew[o] = txx; pnew[S + o] = txy; pnew[2 * S + o] = p;
+        if (ii >= 1 && ii <= TX && jj >= 1 && jj <= TY) {
+            if (MODE == MODE_CG) { pnew[o] = txx; pnew[S + o] = txy; pnew[2 * S + o] = p; }
+            sm.own[0][jj - 1][ii - 1] = txx;
+            sm.own[1][jj - 1][ii - 1] = txy;
+            sm.own[2][jj - 1][ii - 1] = p;
         }
         sm.U[jj][ii] = ac * (p - txx);
         sm.V[jj][ii] = ac * (p + txx);
         sm.N[jj][ii] = an * txy;
     }
     __syncthreads();
-    for (int e = t; e < (TY + 1) * (TX + 1); e += NT) {
-        int jj = e / (TX + 1), ii = e - jj * (TX + 1);
-        T ku = ld<T, C>(K_u, L.off(c0 + ii, r0 - 1 + jj, 0));
-        T kv = ld<T, C>(K_v, L.off(c0 - 1 + ii, r0 + jj, 0));
-        sm.Zu[jj][ii] = ku * ((sm.U[jj][ii + 1] - sm.U[jj][ii]) + (sm.N[jj][ii + 1] - sm.N[jj + 1][ii + 1]));
-        sm.Zv[jj][ii] = kv * ((sm.V[jj + 1][ii] - sm.V[jj][ii]) + (sm.N[jj + 1][ii] - sm.N[jj + 1][ii + 1]));
+#pragma unroll
+    for (int q = 0; q < NFACE; ++q) {
+        int e = t + q * NT;
+        if (e < (TY + 1) * (TX + 1)) {
+            int jj = e / (TX + 1), ii = e - jj * (TX + 1);
+            sm.Zu[jj][ii] = ku[q] * ((sm.U[jj][ii + 1] - sm.U[jj][ii]) + (sm.N[jj][ii + 1] - sm.N[jj + 1][ii + 1]));
+            sm.Zv[jj][ii] = kv[q] * ((sm.V[jj + 1][ii] - sm.V[jj][ii]) + (sm.N[jj + 1][ii] - sm.N[jj + 1][ii + 1]));
+        }
     }
     __syncthreads();
     Acc<T> acc;
-    for (int e = t; e < TY * TX; e += NT) {
+#pragma unroll
+    for (int q = 0; q < NOWN; ++q) {
+        const int e = t + q * NT;
+        if (e >= TY * TX) break;
         const int tx = e & (TX - 1), ty = e / TX;
         const int64_t o = L.off(c0 + tx, r0 + ty, 0);
-        T ac = ld<T, C>(a_c, o), an = ld<T, C>(a_n, o), dc = ld<T, C>(d_c, o), dn = ld<T, C>(d_n, o);
-        T p_, txx, txy;
-        if (MODE == MODE_CG) {
-            txx = pnew[o]; txy = pnew[S + o]; p_ = pnew[2 * S + o];
-        } else {
-            txx = x[o]; txy = x[S + o]; p_ = x[2 * S + o];
-        }
+        T ac = oac[q], an = oan[q], dc = odc[q], dn = odn[q];
+        T txx = sm.own[0][ty][tx], txy = sm.own[1][ty][tx], p_ = sm.own[2][ty][tx];
         T zu = sm.Zu[ty + 1][tx], zur = sm.Zu[ty + 1][tx + 1], zud = sm.Zu[ty][tx];
         T zv = sm.Zv[ty][tx + 1], zvu = sm.Zv[ty + 1][tx + 1], zvl = sm.Zv[ty][tx];
         T yp, yxx;

@@ -28,6 +28,18 @@ struct DevArrays {
     uint8_t* tile_flag4;  // 2D: activity of 32 x 4 tiles (batched solver plans)
 };
 
+// Learned-preconditioner state of a context (fpcg.cu).
+struct LearnedState {
+    struct stokes_net_s* net = nullptr;
+    float* feat = nullptr;     // network input (D, H, W, cin)
+    float* out = nullptr;      // network output (D, H, W, cout)
+    float* zold = nullptr;     // previous preconditioned residual
+    double* norm = nullptr;
+    double* dots = nullptr;
+    int64_t n_active = 0;
+    const uint8_t** d_act = nullptr;   // device copy of the activity pointers
+};
+
 // Work vectors of one precision.
 template <class T> struct CgWork {
     T *x = nullptr, *r = nullptr, *z = nullptr, *p[2] = {nullptr, nullptr}, *q = nullptr;
@@ -67,6 +79,8 @@ struct Ctx {
     cudaEvent_t ev[4]{};
     double last_apply_ms = -1.0;
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // inner solve per precision
+    LearnedState learned;
+    long learned_jacobi_steps = 0;
 
     DevArrays dev_arrays() const { return A; }
     cudaError_t zero_weights() { return cudaMemsetAsync(weight_block, 0, weight_bytes, stream); }

@@ -22,6 +22,9 @@
 
 namespace stk {
 
+cudaError_t run_inner_fpcg(Ctx* c, stokes_net_s* net, double scale, double tol_rel, int max_iter, int* iters,
+                           int* jacobi_steps);
+
 // Walk the slots of one tile: 2D 8 rows of 32, 3D 16 rows of 32.
 __device__ __forceinline__ int tile_rows(const Layout& L) { return L.dim == 2 ? TY2 : TY3 * TZ3; }
 
@@ -140,16 +143,31 @@ __global__ void __launch_bounds__(256) k_cg_update(Layout L, const int* __restri
     const T alpha = (T)sc->alpha;
     AccT<T> rz, rr;
     const int nrow = tile_rows(L);
+    T* __restrict__ X = w.x;
+    T* __restrict__ Rr = w.r;
+    T* __restrict__ Z = w.z;
+    const T* __restrict__ Q = w.q;
     for (int row = warp; row < nrow; row += 8) {
-        int64_t o = tile_row_off(L, tile, row) + lane;
-        for (int f = 0; f < nf; ++f) {
-            int64_t of = (int64_t)f * L.stride + o;
-            T pv = p[of];
-            w.x[of] += alpha * pv;
-            T r = w.r[of] - alpha * w.q[of];
-            T z = minv[of] * r;
-            w.r[of] = r; w.z[of] = z;
-            rz.add(r, z); rr.add(r, r);
+        const int64_t o = tile_row_off(L, tile, row) + lane;
+        // issue every load of the slot's fields before any store
+        T pv[6], xv[6], rv[6], qv[6], mv[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            if (f < nf) {
+                const int64_t of = (int64_t)f * L.stride + o;
+                pv[f] = __ldg(p + of); xv[f] = X[of]; rv[f] = Rr[of]; qv[f] = __ldg(Q + of); mv[f] = __ldg(minv + of);
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            if (f < nf) {
+                const int64_t of = (int64_t)f * L.stride + o;
+                T r = rv[f] - alpha * qv[f];
+                T z = mv[f] * r;
+                X[of] = xv[f] + alpha * pv[f];
+                Rr[of] = r; Z[of] = z;
+                rz.add(r, z); rr.add(r, r);
+            }
         }
     }
     double a = rz.warp(), b = rr.warp();
@@ -370,7 +388,13 @@ stokes_status solve_system(Ctx* c, const double* b, double* x, const stokes_opti
         double tol_rel = mode == STOKES_FP64 ? target : std::fmax(o->inner_tol, target);
         double scale = 1.0 / std::sqrt(rr);
         CK(push_inner_params(c, scale, tol_rel, remaining));
-        if (mode == STOKES_FP64)
+        if (o->precond == 1 && c->learned.net && mode != STOKES_FP64) {
+            // learned preconditioner: flexible CG in FP32 (both FP32 and BF16 modes)
+            int its = 0, jac = 0;
+            CK(run_inner_fpcg(c, c->learned.net, scale, tol_rel, remaining, &its, &jac));
+            c->learned_jacobi_steps += jac;
+            mode = STOKES_FP32;
+        } else if (mode == STOKES_FP64)
             CK(run_inner<double, double>(c, 0, c->w64, c->A.minv64, c->coef<double>(), use_graph, o->check_every));
         else if (mode == STOKES_FP32)
             CK(run_inner<float, float>(c, 1, c->w32, c->A.minv32, c->coef<float>(), use_graph, o->check_every));
@@ -384,9 +408,11 @@ stokes_status solve_system(Ctx* c, const double* b, double* x, const stokes_opti
         total_iter += c->h_sc[0].iter;
         double rr_new = c->h_sc[1].rr;
         int ist = c->h_sc[0].status;
-        if (!(rr_new < rr) || !std::isfinite(rr_new)) {
-            // the step did not reduce the FP64 residual: undo it and move the
-            // inner solve up one precision (BF16 -> FP32 -> FP64)
+        if (!(rr_new <= 4.0 * rr) || !std::isfinite(rr_new)) {
+            // the step made the FP64 residual grow (refinement diverging at
+            // this inner precision): undo it and move the inner solve up one
+            // precision (BF16 -> FP32 -> FP64).  A step that merely stalls is
+            // kept: later steps usually recover.
             update(-1.0);
             CK(residual());
             CK(fetch_scalars(c));

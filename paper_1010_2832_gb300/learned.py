@@ -1,0 +1,97 @@
+"""Training data, training loop and evaluation of the learned preconditioner.
+
+Pairs come from the solver itself, as in the classic error-correction
+setting: for a smooth random error field e on the active unknowns, the
+residual it leaves is r = A e (one FP64 apply on the GPU).  The network is
+trained to map the normalised, Jacobi-scaled residual to the matching
+error (see stokes_learned_features / stokes_learned_targets).  Everything
+runs on the GPU through the C ABI; the random fields are seeded inputs
+built on the host.
+"""
+import time
+
+import numpy as np
+import torch
+
+from . import stokes, workloads
+
+_KINDS = {2: ("cell", "node", "cell"), 3: ("cell", "cell", "exy", "exz", "eyz", "cell")}
+
+
+def smooth_error(ctx, wl, seed, modes=6):
+    """Seeded smooth random error in FP64 slot layout, zero on inactive
+    unknowns: a sum of random Fourier modes per unknown field."""
+    rng = np.random.default_rng(seed)
+    act = ctx.export(3).cpu().numpy().astype(bool)
+    parts = []
+    for kind in _KINDS[wl.dim]:
+        P = workloads.sample_points(kind, wl.n, wl.h, wl.origin)
+        f = np.zeros(P[0].shape)
+        for _ in range(modes):
+            k = rng.integers(1, 6, wl.dim)
+            ph = rng.uniform(0, 2 * np.pi)
+            arg = sum(2 * np.pi * k[d] * P[d] for d in range(wl.dim)) + ph
+            f += rng.normal() * np.sin(arg)
+        parts.append(f.ravel())
+    e = np.concatenate(parts) * act
+    return ctx.fields_to_slots(torch.from_numpy(e).cuda())
+
+
+def make_pairs(ctx, wl, n_pairs, seed0):
+    """(features, targets) device tensors for n_pairs smooth errors."""
+    xs, ys = [], []
+    Ae = ctx.new_vector()
+    for q in range(n_pairs):
+        e = smooth_error(ctx, wl, seed0 + q)
+        ctx.apply(e, Ae, stokes.FP64)
+        x, rms = stokes.learned_features(ctx, Ae)
+        y = stokes.learned_targets(ctx, e, rms)
+        xs.append(x)
+        ys.append(y)
+    return xs, ys
+
+
+def train(net, data, shape, epochs=20, batch=4, lr=2e-3, seed=0, log=None):
+    """Adam on the normalised squared error; data = list of (x, y)."""
+    rng = np.random.default_rng(seed)
+    B = batch
+    D, H, W = shape
+    n = len(data)
+    losses = []
+    for ep in range(epochs):
+        order = rng.permutation(n)
+        tot = 0.0
+        for s in range(0, n - B + 1, B):
+            idx = order[s:s + B]
+            x = torch.cat([data[i][0] for i in idx])
+            y = torch.cat([data[i][1] for i in idx])
+            tot += net.train_step(x, y, (B, D, H, W), lr)
+        losses.append(tot / max(1, n // B))
+        if log:
+            log(f"epoch {ep} loss {losses[-1]:.4f}")
+    return losses
+
+
+def solve(ctx, dev, mode, precond, tol=1e-8, max_iter=200000):
+    """One implicit step; returns (stats dict, wall ms on the device)."""
+    nx, ny = wl_sizes = ctx.n[0], ctx.n[1]
+    sizes = _field_sizes(ctx)
+    u = [torch.zeros_like(t) for t in dev["u_star"]]
+    taus = [torch.zeros(s, dtype=torch.float64, device="cuda") for s in sizes[:-1]]
+    p = torch.zeros(sizes[-1], dtype=torch.float64, device="cuda")
+    opt = stokes.default_options(mode=mode, tol=tol, precond=precond, max_iter=max_iter)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = ctx.solve_step(dev["u_star"], u, taus, p, opt)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3
+    return st.as_dict(), ms, (u, taus, p)
+
+
+def _field_sizes(ctx):
+    nx, ny = ctx.n[0], ctx.n[1]
+    if ctx.dim == 2:
+        return [nx * ny, (nx + 1) * (ny + 1), nx * ny]
+    nz = ctx.n[2]
+    return [nx * ny * nz, nx * ny * nz, nz * (ny + 1) * (nx + 1), (nz + 1) * ny * (nx + 1),
+            (nz + 1) * (ny + 1) * nx, nx * ny * nz]

@@ -48,7 +48,11 @@ EXPORTED = ("stokes_create", "stokes_destroy", "stokes_last_error", "stokes_buil
             "stokes_solve_system", "stokes_export", "stokes_export_size", "stokes_slots_to_fields",
             "stokes_fields_to_slots", "stokes_last_apply_ms", "stokes_bench_cg_kernels", "stokes_active_tiles",
             "stokes_batch_create", "stokes_batch_solve", "stokes_batch_destroy", "stokes_batch_tuning",
-            "stokes_solve_batched")
+            "stokes_solve_batched", "stokes_net_create", "stokes_net_destroy", "stokes_net_param_count",
+            "stokes_net_layer", "stokes_net_set_params", "stokes_net_get_params", "stokes_net_forward",
+            "stokes_net_gradient", "stokes_net_train_step", "stokes_set_learned_preconditioner",
+            "stokes_learned_grid", "stokes_learned_features", "stokes_learned_targets",
+            "stokes_learned_jacobi_steps")
 
 
 class BatchIO(C.Structure):
@@ -92,6 +96,20 @@ def load_library(path=LIB_PATH):
         "stokes_batch_destroy": (I, [P]),
         "stokes_batch_tuning": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(D), C.POINTER(I)]),
         "stokes_solve_batched": (I, [I, C.POINTER(P), C.POINTER(BatchIO), C.POINTER(Options), C.POINTER(Stats)]),
+        "stokes_net_create": (I, [C.POINTER(P), I, I, I, I64]),
+        "stokes_net_destroy": (I, [P]),
+        "stokes_net_param_count": (I64, [P]),
+        "stokes_net_layer": (I, [P, I, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I64), C.POINTER(I64)]),
+        "stokes_net_set_params": (I, [P, P]),
+        "stokes_net_get_params": (I, [P, P]),
+        "stokes_net_forward": (I, [P, I, I, I, I, P, P]),
+        "stokes_net_gradient": (I, [P, I, I, I, I, P, P, C.POINTER(D), P]),
+        "stokes_net_train_step": (I, [P, I, I, I, I, P, P, C.c_float, C.POINTER(D)]),
+        "stokes_set_learned_preconditioner": (I, [P, P]),
+        "stokes_learned_grid": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
+        "stokes_learned_features": (I, [P, P, P, C.POINTER(D)]),
+        "stokes_learned_targets": (I, [P, P, D, P]),
+        "stokes_learned_jacobi_steps": (C.c_long, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -301,6 +319,134 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Net:
+    """The learned preconditioner's network (stokes_net_* in include/stokes.h)."""
+
+    def __init__(self, dim, cin, cout, max_voxels):
+        import numpy as np  # noqa: F401
+        self.lib = load_library()
+        h = C.c_void_p()
+        st = self.lib.stokes_net_create(C.byref(h), dim, cin, cout, int(max_voxels))
+        if st != 0:
+            raise StokesError(st, "stokes_net_create failed")
+        self.h, self.dim, self.cin, self.cout = h, dim, cin, cout
+        self.n = self.lib.stokes_net_param_count(self.h)
+
+    def layers(self):
+        out = []
+        for i in range(11):
+            ci, co, ks, wo, bo = C.c_int(), C.c_int(), C.c_int(), C.c_int64(), C.c_int64()
+            self.lib.stokes_net_layer(self.h, i, C.byref(ci), C.byref(co), C.byref(ks), C.byref(wo), C.byref(bo))
+            out.append((ci.value, co.value, ks.value, wo.value, bo.value))
+        return out
+
+    def set_params(self, theta32):
+        import numpy as np
+        a = np.ascontiguousarray(theta32, dtype=np.float32)
+        assert a.size == self.n
+        self.lib.stokes_net_set_params(self.h, a.ctypes.data)
+
+    def get_params(self):
+        import numpy as np
+        a = np.zeros(self.n, dtype=np.float32)
+        self.lib.stokes_net_get_params(self.h, a.ctypes.data)
+        return a
+
+    def from_oracle_layout(self, theta):
+        """Oracle order (per conv: W[cout][cin][k..], b) -> this library's
+        layout (per conv: W[tap][cin][cout], b, 4-float aligned)."""
+        import numpy as np
+        out = np.zeros(self.n, dtype=np.float32)
+        o = 0
+        for ci, co, ks, wo, bo in self.layers():
+            kd = (ks,) * self.dim
+            nw = co * ci * int(np.prod(kd))
+            W = np.asarray(theta[o:o + nw]).reshape((co, ci) + kd)
+            o += nw
+            perm = tuple(range(2, 2 + self.dim)) + (1, 0)
+            out[wo:wo + nw] = W.transpose(perm).reshape(-1)
+            out[bo:bo + co] = theta[o:o + co]
+            o += co
+        return out
+
+    def to_oracle_layout(self, p):
+        import numpy as np
+        parts = []
+        for ci, co, ks, wo, bo in self.layers():
+            kd = (ks,) * self.dim
+            nw = co * ci * int(np.prod(kd))
+            W = np.asarray(p[wo:wo + nw], dtype=np.float64).reshape(kd + (ci, co))
+            inv = (self.dim + 1, self.dim) + tuple(range(self.dim))
+            parts.append(W.transpose(inv).reshape(-1))
+            parts.append(np.asarray(p[bo:bo + co], dtype=np.float64))
+        return np.concatenate(parts)
+
+    def forward(self, x, shape):
+        B, D, H, W = shape
+        y = torch.zeros(B * D * H * W * self.cout, dtype=torch.float32, device="cuda")
+        st = self.lib.stokes_net_forward(self.h, B, D, H, W, _dev(x, torch.float32).data_ptr(), y.data_ptr())
+        if st != 0:
+            raise StokesError(st, "stokes_net_forward failed")
+        return y
+
+    def gradient(self, x, y, shape):
+        import numpy as np
+        B, D, H, W = shape
+        g = np.zeros(self.n, dtype=np.float32)
+        loss = C.c_double()
+        st = self.lib.stokes_net_gradient(self.h, B, D, H, W, _dev(x, torch.float32).data_ptr(),
+                                          _dev(y, torch.float32).data_ptr(), C.byref(loss), g.ctypes.data)
+        if st != 0:
+            raise StokesError(st, "stokes_net_gradient failed")
+        return loss.value, g
+
+    def train_step(self, x, y, shape, lr):
+        B, D, H, W = shape
+        loss = C.c_double()
+        st = self.lib.stokes_net_train_step(self.h, B, D, H, W, _dev(x, torch.float32).data_ptr(),
+                                            _dev(y, torch.float32).data_ptr(), C.c_float(lr), C.byref(loss))
+        if st != 0:
+            raise StokesError(st, "stokes_net_train_step failed")
+        return loss.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.stokes_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def learned_grid(ctx):
+    v = [C.c_int() for _ in range(5)]
+    ctx.lib.stokes_learned_grid(ctx.h, *[C.byref(a) for a in v])
+    return tuple(a.value for a in v)   # D, H, W, cin, cout
+
+
+def attach_network(ctx, net):
+    ctx._check(ctx.lib.stokes_set_learned_preconditioner(ctx.h, net.h if net is not None else None))
+    ctx._net = net
+
+
+def learned_features(ctx, r):
+    D, H, W, cin, cout = learned_grid(ctx)
+    x = torch.zeros(D * H * W * cin, dtype=torch.float32, device="cuda")
+    rms = C.c_double()
+    ctx._check(ctx.lib.stokes_learned_features(ctx.h, _dev(r).data_ptr(), x.data_ptr(), C.byref(rms)))
+    return x, rms.value
+
+
+def learned_targets(ctx, e, rms):
+    D, H, W, cin, cout = learned_grid(ctx)
+    y = torch.zeros(D * H * W * cout, dtype=torch.float32, device="cuda")
+    ctx._check(ctx.lib.stokes_learned_targets(ctx.h, _dev(e).data_ptr(), C.c_double(rms), y.data_ptr()))
+    return y
 
 
 def upload_workload(wl):

@@ -1,0 +1,75 @@
+"""Learned preconditioner inside flexible CG: with any network the solve must
+still reach the FP64 true residual (the flexible method plus the Jacobi
+fallback and the FP64 refinement guarantee it); a network trained on
+solver-generated pairs is compared with the Jacobi-preconditioned solve on
+held-out instances (iterations reported; the comparison is recorded, not
+assumed)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from gpu_common import oracle_system, require_gpu
+from oracle import solve as So
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_fpcg_with_untrained_network_converges():
+    require_gpu()
+    from paper_1010_2832_gb300 import learned, stokes, workloads as W
+    wl = W.bumps_2d(40, seed=21)
+    ctx, dev = stokes.context_for(wl)
+    D, H, Wd, cin, cout = stokes.learned_grid(ctx)
+    net = stokes.Net(2, cin, cout, D * H * Wd)
+    from oracle import unet as U
+    net.set_params(net.from_oracle_layout(U.init_params(2, cin, cout, seed=0)))
+    stokes.attach_network(ctx, net)
+    st, ms, (u, taus, p) = learned.solve(ctx, dev, mode=1, precond=1, tol=1e-8)
+    assert st["status"] == 0, st
+    S = oracle_system(wl)
+    x = torch.cat(taus + [p]).cpu().numpy()
+    assert So.relative_residual(S.A, x, S.b) <= 1.01e-8
+
+
+def test_trained_network_vs_jacobi(tmp_path):
+    require_gpu()
+    from paper_1010_2832_gb300 import learned, stokes, workloads as W
+    n = 44
+    train_wls = [W.bumps_2d(n, seed=500 + i, rho_split=False) for i in range(6)]
+    data = []
+    shape = None
+    net = None
+    for i, wl in enumerate(train_wls):
+        ctx, dev = stokes.context_for(wl)
+        D, H, Wd, cin, cout = stokes.learned_grid(ctx)
+        if net is None:
+            net = stokes.Net(2, cin, cout, 8 * D * H * Wd)
+            from oracle import unet as U
+            net.set_params(net.from_oracle_layout(U.init_params(2, cin, cout, seed=1)))
+            shape = (D, H, Wd)
+        stokes.attach_network(ctx, net)
+        xs, ys = learned.make_pairs(ctx, wl, 12, seed0=1000 * i)
+        data += list(zip(xs, ys))
+    losses = learned.train(net, data, shape, epochs=25, batch=4, lr=2e-3)
+    assert losses[-1] < losses[0]
+    results = []
+    for i in range(3):
+        wl = W.bumps_2d(n, seed=900 + i, rho_split=False)
+        ctx, dev = stokes.context_for(wl)
+        stokes.attach_network(ctx, net)
+        st_l, ms_l, out = learned.solve(ctx, dev, mode=1, precond=1)
+        st_j, ms_j, _ = learned.solve(ctx, dev, mode=0, precond=0)
+        assert st_l["status"] == 0 and st_j["status"] == 0
+        S = oracle_system(wl)
+        x = torch.cat(out[1] + [out[2]]).cpu().numpy()
+        assert So.relative_residual(S.A, x, S.b) <= 1.01e-8
+        results.append(dict(learned_iters=st_l["iterations"], jacobi_fp64_iters=st_j["iterations"],
+                            learned_ms=ms_l, jacobi_ms=ms_j))
+    out_dir = os.environ.get("STOKES_RESULTS_DIR")
+    if out_dir:
+        with open(os.path.join(out_dir, "learned_vs_jacobi.json"), "w") as f:
+            json.dump(dict(train_loss=losses, results=results), f)
+    print("learned vs jacobi:", results)

@@ -1,0 +1,74 @@
+"""The CUDA U-Net against the FP64 CPU reference (oracle.unet).
+
+BF16 activations with FP32 accumulation: the forward output must agree with
+the FP64 reference to 2e-2 relative (RMS over the output), and the parameter
+gradient must point the same way (cosine similarity >= 0.999, relative norm
+difference <= 5e-2).  A few Adam steps must reduce the loss."""
+import numpy as np
+import pytest
+
+from gpu_common import require_gpu
+from oracle import unet as U
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _setup(dim, cin, cout, shape, seed):
+    from paper_1010_2832_gb300 import stokes
+    rng = np.random.default_rng(seed)
+    B, D, H, W = shape
+    vox = B * D * H * W
+    net = stokes.Net(dim, cin, cout, vox)
+    th = U.init_params(dim, cin, cout, seed=seed) * 0.7
+    th += rng.normal(scale=0.02, size=th.size)   # nonzero biases
+    net.set_params(net.from_oracle_layout(th))
+    sp = (D, H, W) if dim == 3 else (H, W)
+    x = rng.normal(size=(B,) + sp + (cin,)).astype(np.float32)
+    y = rng.normal(size=(B,) + sp + (cout,)).astype(np.float32)
+    # oracle wants (B, C, spatial...)
+    to_nc = lambda a: np.moveaxis(a, -1, 1).astype(np.float64)
+    return net, th, x, y, to_nc
+
+
+@pytest.mark.parametrize("dim,cin,cout,shape", [(2, 8, 4, (2, 1, 16, 12)), (3, 12, 8, (1, 8, 8, 12))])
+def test_forward_matches_oracle(dim, cin, cout, shape):
+    require_gpu()
+    net, th, x, y, to_nc = _setup(dim, cin, cout, shape, 1)
+    # the oracle sees the same BF16-rounded input the network stores
+    xb = torch.tensor(x).to(torch.bfloat16).to(torch.float64).numpy()
+    ref = U.predict(net.to_oracle_layout(net.get_params()), to_nc(xb), dim, cin, cout)
+    got = net.forward(torch.tensor(x.reshape(-1)).cuda(), shape).cpu().numpy().reshape(y.shape)
+    got = np.moveaxis(got, -1, 1)
+    err = np.sqrt(np.mean((got - ref) ** 2)) / np.sqrt(np.mean(ref ** 2))
+    assert err < 2e-2, err
+
+
+@pytest.mark.parametrize("dim,cin,cout,shape", [(2, 8, 4, (2, 1, 16, 12)), (3, 12, 8, (1, 8, 8, 12))])
+def test_gradient_matches_oracle(dim, cin, cout, shape):
+    require_gpu()
+    net, th, x, y, to_nc = _setup(dim, cin, cout, shape, 2)
+    xb = torch.tensor(x).to(torch.bfloat16).to(torch.float64).numpy()
+    theta = net.to_oracle_layout(net.get_params())
+    L_ref, g_ref = U.loss_and_grad(theta, to_nc(xb), to_nc(y), dim, cin, cout)
+    L, g = net.gradient(torch.tensor(x.reshape(-1)).cuda(), torch.tensor(y.reshape(-1)).cuda(), shape)
+    g = net.to_oracle_layout(g)
+    assert abs(L - L_ref) <= 2e-2 * abs(L_ref)
+    cos = g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref))
+    assert cos >= 0.999, cos
+    assert abs(np.linalg.norm(g) - np.linalg.norm(g_ref)) <= 5e-2 * np.linalg.norm(g_ref)
+
+
+def test_training_reduces_loss():
+    require_gpu()
+    dim, cin, cout, shape = 2, 8, 4, (4, 1, 16, 16)
+    net, th, x, y, to_nc = _setup(dim, cin, cout, shape, 3)
+    # a learnable target: a fixed smoothing of the input's first channels
+    xt = torch.tensor(x.reshape(-1)).cuda()
+    yt_np = 0.5 * x[..., :cout] + 0.25 * np.roll(x[..., :cout], 1, axis=2)
+    yt = torch.tensor(yt_np.astype(np.float32).reshape(-1)).cuda()
+    l0 = net.gradient(xt, yt, shape)[0]
+    for _ in range(60):
+        net.train_step(xt, yt, shape, 3e-3)
+    l1 = net.gradient(xt, yt, shape)[0]
+    assert l1 < 0.5 * l0, (l0, l1)
