@@ -165,7 +165,11 @@ typedef struct {
     double inner_tol;  /* relative tolerance of each inner solve (mixed)    */
     int max_outer;     /* cap on refinement steps (mixed)                    */
     int check_every;   /* iterations between host convergence checks        */
-    int precond;       /* 0 = Jacobi (point diagonal)                        */
+    int precond;       /* 0 = Jacobi (point diagonal); 1 = learned network
+                          (flexible CG, see stokes_set_learned_preconditioner);
+                          2 = additive Schwarz, 2D: overlapping patches of
+                          4x4 slots plus a one-slot ring, exact local solves
+                          (BF16-stored inverses, FP32 inner CG)               */
     int use_graph;     /* 1: CG loop in a device-side CUDA graph (conditional
                           while node); 0: host-driven chunks of check_every
                           iterations launched one kernel at a time (for
@@ -336,6 +340,16 @@ stokes_status stokes_learned_features(stokes_ctx ctx, const double* r, float* x,
 stokes_status stokes_learned_targets(stokes_ctx ctx, const double* e, double rms, float* y);
 /* Steps at which the flexible CG fell back to the Jacobi direction. */
 long stokes_learned_jacobi_steps(stokes_ctx ctx);
+
+/* z = M^-1 r for FP32 slot-layout device vectors: which = 0 Jacobi
+ * (z = r / diag A, z = r on inactive unknowns), 2 additive Schwarz (2D):
+ * z = sum_p R_p^T A_p^-1 R_p r over overlapping patches (4x4-slot core plus a
+ * one-slot ring, the patch's active unknowns), inactive unknowns z = r.  The
+ * Schwarz patch inverses are built on first use after each weight build
+ * (stokes_schwarz_setup_ms reports the device time of that build, -1 if
+ * none). */
+stokes_status stokes_apply_preconditioner(stokes_ctx ctx, int which, const float* r, float* z);
+double stokes_schwarz_setup_ms(stokes_ctx ctx);
 
 /* Number of tiles holding an active unknown (2D tiles are 32 x 8 slots,
  * 3D tiles 32 x 4 x 4); every CG kernel launches one CTA per such tile. */

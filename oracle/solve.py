@@ -87,6 +87,38 @@ def pcg(A, b, tol=1e-8, max_iter=100000, x0=None, M_inv=None, true_check=True):
     return x, it, relative_residual(A, x, b)
 
 
+def slot_coordinates_2d(S):
+    """(i, j) slot of every unknown in the oracle's 2D order [txx, txy, p]."""
+    nx, ny = S.inp.n
+    ci = np.tile(np.arange(nx), ny); cj = np.repeat(np.arange(ny), nx)
+    ni = np.tile(np.arange(nx + 1), ny + 1); nj = np.repeat(np.arange(ny + 1), nx + 1)
+    return np.concatenate([ci, ni, ci]), np.concatenate([cj, nj, cj])
+
+
+def additive_schwarz(S, r, core=4, ring=1):
+    """z = sum_p R_p^T (R_p A R_p^T)^-1 R_p r (2D) over the patches whose core
+    (core x core slots) holds an active unknown; patch p takes the active
+    unknowns of its core widened by ``ring`` slots.  Inactive unknowns: z = r.
+    Dense FP64 local solves; the definition of the GPU's Schwarz
+    preconditioner written out."""
+    A = S.A.tocsr()
+    si, sj = slot_coordinates_2d(S)
+    act = S.active
+    z = np.where(act, 0.0, r)
+    nx, ny = S.inp.n
+    for J in range(0, (ny + 1 + core - 1) // core):
+        for I in range(0, (nx + 1 + core - 1) // core):
+            incore = act & (si >= core * I) & (si < core * I + core) & (sj >= core * J) & (sj < core * J + core)
+            if not incore.any():
+                continue
+            m = act & (si >= core * I - ring) & (si < core * I + core + ring) & \
+                (sj >= core * J - ring) & (sj < core * J + core + ring)
+            idx = np.flatnonzero(m)
+            Ap = A[idx][:, idx].toarray()
+            z[idx] += np.linalg.solve(Ap, r[idx])
+    return z
+
+
 def time_pcg_iterations(A, b, iters):
     """Wall time of ``iters`` iterations of ``pcg`` (no convergence test), for
     the CPU baseline.  Returns seconds."""

@@ -15,7 +15,21 @@ void set_error(Ctx* c, const std::string& m) { c->err = m; }
 cudaError_t launch_unpack(Ctx* c, const double* slots, double* const* fields, int to_fields);
 void apply_set_attributes();
 cudaError_t bench_cg_kernels(Ctx* c, int precision, int launches, double* ms_apply, double* ms_update);
+cudaError_t apply_preconditioner(Ctx* c, int which, const float* r, float* z);
+double schwarz_setup_ms(Ctx* c);
 }  // namespace stk
+
+extern "C" stokes_status stokes_apply_preconditioner(stokes_ctx h, int which, const float* r, float* z) {
+    if (!h || !r || !z || r == z || (which != 0 && which != 2)) return STOKES_ERR_ARG;
+    Ctx& c = h->c;
+    if (!c.have_weights) { c.err = "stokes_build_weights has not run"; return STOKES_ERR_STATE; }
+    if (which == 2 && c.L.dim != 2) { c.err = "the Schwarz preconditioner is 2D only"; return STOKES_ERR_ARG; }
+    cudaError_t e = apply_preconditioner(&c, which, r, z);
+    if (e != cudaSuccess) { c.err = std::string("preconditioner failed: ") + cudaGetErrorString(e); return STOKES_ERR_CUDA; }
+    return STOKES_OK;
+}
+
+extern "C" double stokes_schwarz_setup_ms(stokes_ctx h) { return h ? schwarz_setup_ms(&h->c) : -1.0; }
 
 extern "C" stokes_status stokes_bench_cg_kernels(stokes_ctx h, int precision, int launches, double* ms_apply,
                                                  double* ms_update) {
@@ -191,6 +205,8 @@ stokes_status stokes_destroy(stokes_ctx h) {
     for (auto& ge : c.graph)
         if (ge) cudaGraphExecDestroy(ge);
     for (void* p : c.allocs) cudaFree(p);
+    for (void* p : c.sw_allocs) cudaFree(p);
+    delete c.sw;
     if (c.h_sc) cudaFreeHost(c.h_sc);
     for (auto& ev : c.ev)
         if (ev) cudaEventDestroy(ev);
@@ -223,6 +239,8 @@ stokes_status stokes_build_weights(stokes_ctx h, const double* phiL, const doubl
         if (!mu[s]) { c.err = "null viscosity array"; return STOKES_ERR_ARG; }
     for (auto& ge : c.graph)
         if (ge) { cudaGraphExecDestroy(ge); ge = nullptr; }
+    c.sw_ready = false;
+    c.learned.net = nullptr;
     cudaError_t e = launch_build_weights(&c, phiL, phiS, rho, mu, ubc);
     if (e != cudaSuccess) {
         c.err = std::string("weight build failed: ") + cudaGetErrorString(e);

@@ -78,9 +78,14 @@ struct Ctx {
     double* y64 = nullptr;       // scratch
     cudaEvent_t ev[4]{};
     double last_apply_ms = -1.0;
-    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // inner solve per precision
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // inner solve per precision (+ Schwarz)
     LearnedState learned;
     long learned_jacobi_steps = 0;
+    // additive Schwarz preconditioner (2D), rebuilt lazily after each weight build
+    struct SchwarzPlan* sw = nullptr;
+    std::vector<void*> sw_allocs;
+    bool sw_ready = false;
+    double sw_setup_ms = 0.0;
 
     DevArrays dev_arrays() const { return A; }
     cudaError_t zero_weights() { return cudaMemsetAsync(weight_block, 0, weight_bytes, stream); }

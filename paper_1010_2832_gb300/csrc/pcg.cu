@@ -184,6 +184,144 @@ __global__ void __launch_bounds__(256) k_cg_update(Layout L, const int* __restri
     });
 }
 
+}  // namespace stk
+#include "schwarz.cuh"
+namespace stk {
+
+__global__ void k_jacobi_apply(int64_t n, const float* r, const float* minv, float* z) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) z[e] = minv[e] * r[e];
+}
+
+// Schwarz-preconditioned CG (2D, FP32 vectors).  init: r = scale r64, x = 0,
+// p_old = 0 (z follows from the patch solves); finish: gather z, r.z, r.r and
+// the CG bookkeeping (INIT: start values; else as in k_cg_update).
+__global__ void __launch_bounds__(256) k_sw_init(Layout L, const int* __restrict__ tiles, const double* r64,
+                                                 CgWork<float> w, const CgScalars* sc) {
+    const int tile = tiles[blockIdx.x];
+    const int c0 = (tile % L.ntx) * TX, r0 = (tile / L.ntx) * TY2;
+    const int64_t o = L.off(c0 + (threadIdx.x & 31), r0 + (threadIdx.x >> 5), 0);
+    const double scale = sc->scale;
+    for (int f = 0; f < 3; ++f) {
+        const int64_t of = (int64_t)f * L.stride + o;
+        w.r[of] = (float)(r64[of] * scale);
+        w.x[of] = 0.f;
+        w.p[0][of] = 0.f;
+    }
+}
+
+template <int INIT>
+__global__ void __launch_bounds__(256) k_sw_finish(Layout L, const int* __restrict__ tiles, DevArrays D,
+                                                   SchwarzPlan P, CgWork<float> w, CgScalars* sc, double* partial,
+                                                   unsigned* counter, int nblocks, cudaGraphConditionalHandle h,
+                                                   int use_cond) {
+    if (!INIT && sc->done) {
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+        return;
+    }
+    const int tile = tiles[blockIdx.x];
+    const int c0 = (tile % L.ntx) * TX, r0 = (tile / L.ntx) * TY2;
+    double rz = 0.0, rr = 0.0;
+    schwarz_gather_slot(L, D, P, w.r, w.z, c0 + (threadIdx.x & 31), r0 + (threadIdx.x >> 5), rz, rr);
+    block_partial2(warp_sum(rz), warp_sum(rr), partial, counter, nblocks, [&](double trz, double trr) {
+        if (INIT) {
+            sc->rz = trz; sc->rr = trr; sc->rr0 = trr;
+            sc->tol2 = sc->tol_rel * sc->tol_rel * trr;
+            sc->beta = 0.0; sc->iter = 0; sc->status = 0;
+            sc->done = (trr <= sc->tol2 || trr == 0.0) ? 1 : 0;
+            if (!isfinite(trr)) { sc->done = 1; sc->status = STOKES_ERR_NONFINITE; }
+        } else {
+            sc->rr = trr;
+            sc->iter += 1;
+            if (!isfinite(trr) || !isfinite(trz)) { sc->done = 1; sc->status = STOKES_ERR_NONFINITE; }
+            else if (trr <= sc->tol2) { sc->done = 1; }
+            else if (!(trz > 0.0)) { sc->done = 1; sc->status = STOKES_ERR_BREAKDOWN; }
+            else if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = STOKES_ERR_NOT_CONVERGED; }
+            sc->beta = trz / sc->rz;
+            sc->rz = trz;
+        }
+        if (use_cond) cudaGraphSetConditional(h, sc->done ? 0u : 1u);
+    });
+}
+
+// Patch plan and local inverses (after every weight build, on first use).
+static cudaError_t schwarz_build(Ctx* c) {
+    const Layout& L = c->L;
+    cudaError_t e;
+    for (void* p : c->sw_allocs) cudaFree(p);
+    c->sw_allocs.clear();
+    if (!c->sw) c->sw = new SchwarzPlan();
+    SchwarzPlan& P = *c->sw;
+    P.npx = (L.nx + 1 + PB - 1) / PB;
+    P.npy = (L.ny + 1 + PB - 1) / PB;
+    const int ng = P.npx * P.npy;
+    auto al = [&](void** p, size_t bytes) -> cudaError_t {
+        cudaError_t r = cudaMalloc(p, bytes ? bytes : 16);
+        if (r == cudaSuccess) c->sw_allocs.push_back(*p);
+        return r;
+    };
+    int* dflag = nullptr;
+    if ((e = al((void**)&dflag, sizeof(int) * ng)) != cudaSuccess) return e;
+    k_schwarz_mark<<<dim3((P.npx + 127) / 128, P.npy), 128, 0, c->stream>>>(L, c->A, P.npx, P.npy, dflag);
+    std::vector<int> flag(ng), pid(ng, -1), corner;
+    if ((e = cudaMemcpyAsync(flag.data(), dflag, sizeof(int) * ng, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+        return e;
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
+    for (int J = 0; J < P.npy; ++J)
+        for (int I = 0; I < P.npx; ++I)
+            if (flag[J * P.npx + I]) { pid[J * P.npx + I] = (int)corner.size(); corner.push_back(I | (J << 16)); }
+    P.np = (int)corner.size();
+    const size_t np = std::max(1, P.np);
+    if ((e = al((void**)&P.pid, sizeof(int) * ng)) != cudaSuccess) return e;
+    if ((e = al((void**)&P.corner, sizeof(int) * np)) != cudaSuccess) return e;
+    if ((e = al((void**)&P.nloc, sizeof(int) * np)) != cudaSuccess) return e;
+    if ((e = al((void**)&P.lmap, sizeof(short) * np * PMAX)) != cudaSuccess) return e;
+    if ((e = al((void**)&P.inv, sizeof(__nv_bfloat16) * np * PMAX * PMAX)) != cudaSuccess) return e;
+    if ((e = al((void**)&P.ybuf, sizeof(float) * np * PMAX)) != cudaSuccess) return e;
+    cudaMemcpyAsync(P.pid, pid.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, c->stream);
+    if (P.np) cudaMemcpyAsync(P.corner, corner.data(), sizeof(int) * P.np, cudaMemcpyHostToDevice, c->stream);
+    cudaMemsetAsync(P.ybuf, 0, sizeof(float) * np * PMAX, c->stream);
+    const int smem = (2 * PMAX * PMAX + PMAX) * (int)sizeof(float);
+    cudaFuncSetAttribute(k_schwarz_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaEvent_t a, b;
+    cudaEventCreate(&a); cudaEventCreate(&b);
+    cudaEventRecord(a, c->stream);
+    if (P.np) k_schwarz_setup<<<P.np, 256, smem, c->stream>>>(L, c->A, c->A.coef32, P);
+    cudaEventRecord(b, c->stream);
+    if ((e = cudaEventSynchronize(b)) != cudaSuccess) return e;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a); cudaEventDestroy(b);
+    c->sw_setup_ms = ms;
+    c->sw_ready = true;
+    return cudaGetLastError();
+}
+
+static void schwarz_body(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond, int parity) {
+    const Layout& L = c->L;
+    const int nb = c->ntiles_active;
+    CgWork<float>& w = c->w32;
+    ApplyArgs a{};
+    a.pold = w.p[parity];
+    a.pnew = w.p[parity ^ 1];
+    a.partial = c->partial;
+    a.counter = c->counter;
+    a.sc = c->sc;
+    launch_apply_mode<float, float>(L, c->tiles, nb, c->coef<float>(), w.z, w.q, MODE_CG, a, s);
+    k_cg_xr<<<nb, 256, 0, s>>>(L, c->tiles, c->nf, w, w.p[parity ^ 1], c->sc);
+    if (c->sw->np) k_schwarz_gemv<<<c->sw->np, 128, 0, s>>>(L, *c->sw, w.r, c->sc);
+    k_sw_finish<0><<<nb, 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc, c->partial, c->counter, nb, h, use_cond);
+}
+
+static void schwarz_start(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
+    const Layout& L = c->L;
+    const int nb = c->ntiles_active;
+    CgWork<float>& w = c->w32;
+    k_sw_init<<<nb, 256, 0, s>>>(L, c->tiles, c->w64.r, w, c->sc);
+    if (c->sw->np) k_schwarz_gemv<<<c->sw->np, 128, 0, s>>>(L, *c->sw, w.r, c->sc);
+    k_sw_finish<1><<<nb, 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc, c->partial, c->counter, nb, h, use_cond);
+}
+
 // x64 += sign * d / scale (refinement update; sign = -1 undoes it), over active tiles
 template <class T>
 __global__ void __launch_bounds__(256) k_ir_update(Layout L, const int* __restrict__ tiles, int nf, double* x64,
@@ -322,6 +460,68 @@ static cudaError_t run_inner(Ctx* c, int prec_slot, CgWork<T>& w, const T* minv,
     return cudaGetLastError();
 }
 
+// Inner Schwarz-preconditioned CG solve (FP32 vectors): graph with a
+// conditional while node, or host-driven chunks.
+static cudaError_t run_inner_schwarz(Ctx* c, int use_graph, int chunk) {
+    cudaError_t e;
+    if (!c->sw_ready && (e = schwarz_build(c)) != cudaSuccess) return e;
+    cudaStream_t s = c->stream;
+    if (use_graph) {
+        cudaGraphExec_t& ge = c->graph[3];
+        if (!ge) {
+            cudaGraph_t g = nullptr;
+            if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
+            cudaGraphConditionalHandle h;
+            if ((e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+            if ((e = cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+                cudaSuccess)
+                return e;
+            schwarz_start(c, s, h, 1);
+            cudaGraph_t cap = nullptr;
+            if ((e = cudaStreamEndCapture(s, &cap)) != cudaSuccess) return e;
+            // the conditional node follows every node without dependents
+            size_t na = 0;
+            cudaGraphGetNodes(g, nullptr, &na);
+            std::vector<cudaGraphNode_t> all(na), leaves;
+            cudaGraphGetNodes(g, all.data(), &na);
+            for (auto nd : all) {
+                size_t nd_out = 0;
+                cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &nd_out);
+                if (nd_out == 0) leaves.push_back(nd);
+            }
+            size_t nn = leaves.size();
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t cond;
+            if ((e = cudaGraphAddNode(&cond, g, leaves.data(), nullptr, nn, &cp)) != cudaSuccess) return e;
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+                cudaSuccess)
+                return e;
+            schwarz_body(c, s, h, 1, 0);
+            schwarz_body(c, s, h, 1, 1);
+            cudaGraph_t cap2 = nullptr;
+            if ((e = cudaStreamEndCapture(s, &cap2)) != cudaSuccess) return e;
+            e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaGraphLaunch(ge, s);
+    }
+    cudaGraphConditionalHandle h0 = 0;
+    schwarz_start(c, s, h0, 0);
+    chunk = chunk < 2 ? 2 : (chunk + 1) & ~1;
+    for (;;) {
+        for (int k = 0; k < chunk; ++k) schwarz_body(c, s, h0, 0, k & 1);
+        if ((e = fetch_scalars(c)) != cudaSuccess) return e;
+        if (c->h_sc[0].done) break;
+    }
+    return cudaGetLastError();
+}
+
 static cudaError_t push_inner_params(Ctx* c, double scale, double tol_rel, int max_iter) {
     CgScalars& h = c->h_sc[0];
     std::memset(&h, 0, sizeof(h));
@@ -388,7 +588,11 @@ stokes_status solve_system(Ctx* c, const double* b, double* x, const stokes_opti
         double tol_rel = mode == STOKES_FP64 ? target : std::fmax(o->inner_tol, target);
         double scale = 1.0 / std::sqrt(rr);
         CK(push_inner_params(c, scale, tol_rel, remaining));
-        if (o->precond == 1 && c->learned.net && mode != STOKES_FP64) {
+        if (o->precond == 2 && L.dim == 2 && mode != STOKES_FP64) {
+            // additive Schwarz preconditioner, FP32 inner CG
+            CK(run_inner_schwarz(c, use_graph, o->check_every));
+            mode = STOKES_FP32;
+        } else if (o->precond == 1 && c->learned.net && mode != STOKES_FP64) {
             // learned preconditioner: flexible CG in FP32 (both FP32 and BF16 modes)
             int its = 0, jac = 0;
             CK(run_inner_fpcg(c, c->learned.net, scale, tol_rel, remaining, &its, &jac));
@@ -444,6 +648,32 @@ stokes_status solve_system(Ctx* c, const double* b, double* x, const stokes_opti
     return (stokes_status)status;
 #undef CK
 }
+
+// z = M^-1 r for a FP32 slot-layout r: Jacobi (0) or additive Schwarz (2, 2D).
+cudaError_t apply_preconditioner(Ctx* c, int which, const float* r, float* z) {
+    const Layout& L = c->L;
+    cudaStream_t s = c->stream;
+    const int64_t V = c->vec_elems();
+    cudaError_t e;
+    if (which == 0) {
+        k_jacobi_apply<<<(unsigned)((V + 255) / 256), 256, 0, s>>>(V, r, c->A.minv32, z);
+        return cudaGetLastError();
+    }
+    if (L.dim != 2) return cudaErrorInvalidValue;
+    if (!c->sw_ready && (e = schwarz_build(c)) != cudaSuccess) return e;
+    if ((e = push_inner_params(c, 1.0, 0.0, 1)) != cudaSuccess) return e;
+    // inactive tiles: identity on real slots (r is zero on padding)
+    if ((e = cudaMemcpyAsync(z, r, sizeof(float) * V, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+    CgWork<float> w{};
+    w.r = (float*)r;
+    w.z = z;
+    const int nb = c->ntiles_active;
+    if (c->sw->np) k_schwarz_gemv<<<c->sw->np, 128, 0, s>>>(L, *c->sw, r, c->sc);
+    if (nb) k_sw_finish<1><<<nb, 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc, c->partial, c->counter, nb, 0, 0);
+    return cudaGetLastError();
+}
+
+double schwarz_setup_ms(Ctx* c) { return c->sw_ready ? c->sw_setup_ms : -1.0; }
 
 // Time real CG iterations kernel by kernel: r = b (the last right-hand side),
 // then ``launches`` x [apply in CG mode, update] with CUDA events around each

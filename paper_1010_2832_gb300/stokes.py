@@ -52,7 +52,7 @@ EXPORTED = ("stokes_create", "stokes_destroy", "stokes_last_error", "stokes_buil
             "stokes_net_layer", "stokes_net_set_params", "stokes_net_get_params", "stokes_net_forward",
             "stokes_net_gradient", "stokes_net_train_step", "stokes_set_learned_preconditioner",
             "stokes_learned_grid", "stokes_learned_features", "stokes_learned_targets",
-            "stokes_learned_jacobi_steps")
+            "stokes_learned_jacobi_steps", "stokes_apply_preconditioner", "stokes_schwarz_setup_ms")
 
 
 class BatchIO(C.Structure):
@@ -110,6 +110,8 @@ def load_library(path=LIB_PATH):
         "stokes_learned_features": (I, [P, P, P, C.POINTER(D)]),
         "stokes_learned_targets": (I, [P, P, D, P]),
         "stokes_learned_jacobi_steps": (C.c_long, [P]),
+        "stokes_apply_preconditioner": (I, [P, I, P, P]),
+        "stokes_schwarz_setup_ms": (D, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -260,6 +262,13 @@ class StokesContext:
 
     def active_tiles(self):
         return self.lib.stokes_active_tiles(self.h)
+
+    def apply_preconditioner(self, which, r32, z32):
+        self._check(self.lib.stokes_apply_preconditioner(self.h, which, _dev(r32, torch.float32).data_ptr(),
+                                                         _dev(z32, torch.float32).data_ptr()))
+
+    def schwarz_setup_ms(self):
+        return self.lib.stokes_schwarz_setup_ms(self.h)
 
     def field_vector_length(self):
         nx, ny = self.n[0], self.n[1]

@@ -227,3 +227,24 @@ def test_pcg_matches_direct():
     x, it, rr = So.pcg(S.A, S.b, tol=1e-13)
     assert rr <= 1e-13
     assert np.abs(x - xd).max() <= 1e-9 * np.abs(xd).max()
+
+
+def test_additive_schwarz_single_patch_is_exact_inverse():
+    """A grid small enough for one patch to hold every unknown: the Schwarz
+    operator is A^-1 on the active unknowns."""
+    wl = W.random_small((3, 3), seed=2)
+    S = _system(wl)
+    r = np.random.default_rng(0).normal(size=S.A.shape[0]) * S.active
+    z = So.additive_schwarz(S, r)
+    x = spla.spsolve(S.A.tocsc(), r)
+    assert np.allclose(z, x, rtol=1e-10, atol=1e-12 * np.abs(x).max())
+
+
+def test_additive_schwarz_is_symmetric_positive():
+    S = _system(W.bumps_2d(20, seed=3))
+    rng = np.random.default_rng(1)
+    a = rng.normal(size=S.A.shape[0]) * S.active
+    b = rng.normal(size=S.A.shape[0]) * S.active
+    Ma, Mb = So.additive_schwarz(S, a), So.additive_schwarz(S, b)
+    assert abs(Ma @ b - a @ Mb) <= 1e-10 * np.linalg.norm(Ma) * np.linalg.norm(b)
+    assert a @ Ma > 0
