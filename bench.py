@@ -147,8 +147,11 @@ def run_ours(args, rank, world):
     u_out = [torch.zeros_like(t) for t in d["u_star"]]
     taus = [torch.zeros(s, dtype=torch.float64, device=dev) for s in sizes[:-1]]
     p = torch.zeros(sizes[-1], dtype=torch.float64, device=dev)
+    precond = {"jacobi": 0, "schwarz": 2}[args.precond]
+    if wl.dim != 2:
+        precond = 0                    # the Schwarz preconditioner is 2D only
     opt = stokes.default_options(mode=mode_id(args.mode), tol=args.tol, inner_tol=args.inner_tol,
-                                 use_graph=0 if args.no_graph else 1)
+                                 use_graph=0 if args.no_graph else 1, precond=precond)
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device=dev)
 
     def step():
@@ -231,6 +234,7 @@ def run_ours(args, rank, world):
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 stencil/CG inside f64 refinement" if prec else "f64", "data": "synthetic (seeded)",
         "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "mode": args.mode,
+                   "preconditioner": ["jacobi", "learned", "schwarz"][precond],
                    "tol": args.tol, "inner_tol": args.inner_tol, "l2": "flushed (512 MB write) before each step",
                    "parallelism": f"replicas x{world}"},
         "solver": {"iterations": iters, "outer": outer, "rel_residual": max(s["rel_residual"] for s in stats),
@@ -275,7 +279,8 @@ def cpu_sample(wl, n_iter_fp64, budget_s=12.0):
                       f"Jacobi-PCG count on the GPU for the same system)"}
 
 
-def fp64_iterations(wl):
+def fp64_iterations(wl, with_time=False):
+    """Plain FP64 Jacobi-PCG on the same system: iterations (and device ms)."""
     import torch
     from paper_1010_2832_gb300 import stokes
     ctx, d = stokes.context_for(wl)
@@ -284,6 +289,8 @@ def fp64_iterations(wl):
     ctx.rhs(d["u_star"], b)
     st = ctx.solve_system(b, x, stokes.default_options(mode=0, tol=1e-8))
     torch.cuda.synchronize()
+    if with_time:
+        return st.iterations, st.ms_solve, st.status
     return st.iterations
 
 
@@ -321,6 +328,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bumps1024", choices=list(WORKLOADS))
     ap.add_argument("--mode", default="fp32", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--precond", default="schwarz", choices=["jacobi", "schwarz"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--flush-mb", type=int, default=512)
@@ -344,7 +352,9 @@ def main():
     out, wl = run_ours(args, rank, world)
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            n_it = fp64_iterations(wl)
+            n_it, ms64, st64 = fp64_iterations(wl, with_time=True)
+            out["plain_fp64_pcg"] = {"iterations": n_it, "ms_solve": ms64, "status": st64,
+                                     "note": "plain FP64 Jacobi-PCG on the same system (solve only)"}
             out["cpu_baseline"] = cpu_sample(wl, n_it)
             out["solver"]["fp64_pcg_iterations"] = n_it
         except Exception as e:  # the baseline must not hide the GPU result

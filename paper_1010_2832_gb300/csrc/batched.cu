@@ -569,12 +569,18 @@ stokes_status stokes_batch_create(stokes_batch* out, int n, const stokes_ctx* ct
     if (e == cudaSuccess) e = cudaMalloc(&b->d_g, sizeof(BGlobal));
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
-    // each context's right-hand side must hold something finite for tuning
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_st0, n * sizeof(BState));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_g0, sizeof(BGlobal));
+    // tuning runs real CG iterations: give every instance a nonzero
+    // right-hand side (the Jacobi diagonal; every solve overwrites it)
     for (int i = 0; i < n && e == cudaSuccess; ++i)
-        e = cudaMemsetAsync(b->c[i]->b64, 0, sizeof(double) * b->c[i]->vec_elems(), b->s);
+        e = cudaMemcpyAsync(b->c[i]->b64, b->c[i]->A.minv64, sizeof(double) * b->c[i]->vec_elems(),
+                            cudaMemcpyDeviceToDevice, b->s);
     if (e == cudaSuccess) e = autotune(b, tune_cache);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
     if (e != cudaSuccess) {
+        if (std::getenv("STOKES_VERBOSE")) std::fprintf(stderr, "stokes_batch_create: %s\n", cudaGetErrorString(e));
+        cudaGetLastError();   // leave no pending error for later calls
         stokes_batch_destroy(b);
         return STOKES_ERR_CUDA;
     }

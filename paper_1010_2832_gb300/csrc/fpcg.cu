@@ -15,6 +15,8 @@
 // falls back to the Jacobi direction for that step.  Vectors are FP32; the
 // refinement loop around it (pcg.cu) recomputes the true residual in FP64.
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 #include "internal.cuh"
@@ -279,6 +281,10 @@ cudaError_t run_inner_fpcg(Ctx* c, stokes_net_s* net, double scale, double tol_r
         cudaMemcpyAsync(&back, c->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
         ++it;
+        const bool verbose = std::getenv("STOKES_VERBOSE") != nullptr;
+        if (verbose && (it <= 5 || it % 100 == 0 || back.done))
+            std::fprintf(stderr, "[stokes] fpcg it %d rr/rr0 %.3e r.z %.3e r.zold %.3e alpha %.3e pq %.3e done %d\n", it,
+                         h3[2] / rr0, h3[0], h3[1], back.alpha, back.pq, back.done);
         if (back.done) break;   // p.Ap <= 0: breakdown
         rr = h3[2];
         double rz_new = h3[0], rz_old = h3[1];

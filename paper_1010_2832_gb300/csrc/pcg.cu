@@ -15,6 +15,8 @@
 // scratch with the FP64 operator; stop when ||r64|| <= tol ||b||.  In FP64
 // mode the inner solve is FP64 CG and normally one outer step suffices.
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 #include "internal.cuh"
@@ -612,6 +614,9 @@ stokes_status solve_system(Ctx* c, const double* b, double* x, const stokes_opti
         total_iter += c->h_sc[0].iter;
         double rr_new = c->h_sc[1].rr;
         int ist = c->h_sc[0].status;
+        if (std::getenv("STOKES_VERBOSE"))
+            std::fprintf(stderr, "[stokes] outer %d mode %d precond %d inner iters %d status %d rel %.3e -> %.3e\n",
+                         outer, mode, o->precond, c->h_sc[0].iter, ist, std::sqrt(rr / bb), std::sqrt(rr_new / bb));
         if (!(rr_new <= 4.0 * rr) || !std::isfinite(rr_new)) {
             // the step made the FP64 residual grow (refinement diverging at
             // this inner precision): undo it and move the inner solve up one

@@ -34,14 +34,21 @@ __host__ __device__ inline int64_t vox(const Shape& s) { return (int64_t)s.B * s
 constexpr int CT_X = 8, CT_Y = 8, CT_Z3 = 4;     // 3D tile 8x8x4 = 256 voxels
 constexpr int CT2_X = 16, CT2_Y = 16;           // 2D tile 16x16
 
-// ---- convolution (forward, and data gradient with prepared weights) ------
-template <int KZ, int COUT>
-__global__ void __launch_bounds__(256) k_conv(const __nv_bfloat16* __restrict__ X, Shape s, int cin,
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(float v) { return v; }
+template <class T> __device__ __forceinline__ T zero_of();
+template <> __device__ __forceinline__ __nv_bfloat16 zero_of<__nv_bfloat16>() { return __float2bfloat16(0.f); }
+template <> __device__ __forceinline__ float zero_of<float>() { return 0.f; }
+
+// ---- convolution (forward on BF16 activations; data gradient on FP32 ------
+// gradients with prepared weights)
+template <class TIN, int KZ, int COUT>
+__global__ void __launch_bounds__(256) k_conv(const TIN* __restrict__ X, Shape s, int cin,
                                               const float* __restrict__ Wt, const float* __restrict__ bias,
                                               int relu, __nv_bfloat16* __restrict__ Yb, float* __restrict__ Yf,
                                               int ksize) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __nv_bfloat16* sx = reinterpret_cast<__nv_bfloat16*>(smraw);
+    TIN* sx = reinterpret_cast<TIN*>(smraw);
     const int TXc = KZ == 3 ? CT_X : CT2_X, TYc = KZ == 3 ? CT_Y : CT2_Y, TZc = KZ == 3 ? CT_Z3 : 1;
     const int R = ksize / 2;                 // halo radius (1 for 3x3, 0 for 1x1)
     const int kz = KZ == 3 ? ksize : 1;
@@ -59,7 +66,7 @@ __global__ void __launch_bounds__(256) k_conv(const __nv_bfloat16* __restrict__ 
         int c = e % cin, v = e / cin;
         int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
         int gx = x0 + hx - R, gy = y0 + hy - R, gz = z0 + hz - zr;
-        __nv_bfloat16 val = __float2bfloat16(0.f);
+        TIN val = zero_of<TIN>();
         if (gx >= 0 && gx < s.W && gy >= 0 && gy < s.H && gz >= 0 && gz < s.D)
             val = X[((((int64_t)b * s.D + gz) * s.H + gy) * s.W + gx) * cin + c];
         sx[v * cin + c] = val;
@@ -75,10 +82,10 @@ __global__ void __launch_bounds__(256) k_conv(const __nv_bfloat16* __restrict__ 
     for (int dz = 0; dz < kz; ++dz)
         for (int dy = 0; dy < ksize; ++dy)
             for (int dx = 0; dx < ksize; ++dx, ++tap) {
-                const __nv_bfloat16* xin = sx + (((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * cin;
+                const TIN* xin = sx + (((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * cin;
                 const float* w = Wt + (int64_t)tap * cin * COUT;
                 for (int ci = 0; ci < cin; ++ci) {
-                    float v = __bfloat162float(xin[ci]);
+                    float v = to_f(xin[ci]);
                     const float4* w4 = reinterpret_cast<const float4*>(w + ci * COUT);
 #pragma unroll
                     for (int q = 0; q < COUT / 4; ++q) {
@@ -320,17 +327,17 @@ namespace {
 
 int conv_cout_template_ok(int c) { return c == 4 || c == 8 || c == 12 || c == 16 || c == 24 || c == 32 || c == 48; }
 
-template <int KZ>
-cudaError_t conv_launch(stokes_net_s* n, const __nv_bfloat16* X, Shape s, int cin, const float* W, const float* b,
+template <int KZ, class TIN>
+cudaError_t conv_launch(stokes_net_s* n, const TIN* X, Shape s, int cin, const float* W, const float* b,
                         int relu, __nv_bfloat16* Yb, float* Yf, int cout, int ks) {
     const int TXc = KZ == 3 ? CT_X : CT2_X, TYc = KZ == 3 ? CT_Y : CT2_Y, TZc = KZ == 3 ? CT_Z3 : 1;
     const int R = ks / 2;
-    size_t smem = (size_t)(TXc + 2 * R) * (TYc + 2 * R) * (TZc + (KZ == 3 ? 2 * R : 0)) * cin * 2;
+    size_t smem = (size_t)(TXc + 2 * R) * (TYc + 2 * R) * (TZc + (KZ == 3 ? 2 * R : 0)) * cin * sizeof(TIN);
     unsigned grid = (unsigned)((int64_t)s.B * ((s.D + TZc - 1) / TZc) * ((s.H + TYc - 1) / TYc) * ((s.W + TXc - 1) / TXc));
 #define CASE(C)                                                                                             \
     case C:                                                                                                 \
-        cudaFuncSetAttribute(k_conv<KZ, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
-        k_conv<KZ, C><<<grid, 256, smem, n->s>>>(X, s, cin, W, b, relu, Yb, Yf, ks);                        \
+        cudaFuncSetAttribute(k_conv<TIN, KZ, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
+        k_conv<TIN, KZ, C><<<grid, 256, smem, n->s>>>(X, s, cin, W, b, relu, Yb, Yf, ks);                   \
         break;
     switch (cout) {
         CASE(4) CASE(8) CASE(12) CASE(16) CASE(24) CASE(32) CASE(48)
@@ -354,8 +361,11 @@ cudaError_t wgrad_launch(stokes_net_s* n, const __nv_bfloat16* X, Shape s, int c
 
 cudaError_t conv(stokes_net_s* n, int li, const __nv_bfloat16* X, Shape s, int relu, __nv_bfloat16* Yb, float* Yf) {
     const Conv& c = n->L[li];
-    if (n->KZ == 3) return conv_launch<3>(n, X, s, c.cin, n->theta + c.w_off, n->theta + c.b_off, relu, Yb, Yf, c.cout, c.ks);
-    return conv_launch<1>(n, X, s, c.cin, n->theta + c.w_off, n->theta + c.b_off, relu, Yb, Yf, c.cout, c.ks);
+    if (n->KZ == 3)
+        return conv_launch<3, __nv_bfloat16>(n, X, s, c.cin, n->theta + c.w_off, n->theta + c.b_off, relu, Yb, Yf,
+                                             c.cout, c.ks);
+    return conv_launch<1, __nv_bfloat16>(n, X, s, c.cin, n->theta + c.w_off, n->theta + c.b_off, relu, Yb, Yf,
+                                         c.cout, c.ks);
 }
 
 // data gradient of layer li: dX = conv(dY, flipped W) (no bias, no ReLU)
@@ -363,12 +373,9 @@ cudaError_t conv_dgrad(stokes_net_s* n, int li, const float* dY, Shape s, float*
     const Conv& c = n->L[li];
     int taps = (n->KZ == 3 ? c.ks : 1) * c.ks * c.ks;
     k_flip_weights<<<nblk(c.nw), 256, 0, n->s>>>(n->theta + c.w_off, taps, c.cin, c.cout, n->wflip);
-    // dY to BF16 (the conv kernel reads BF16), staged in g_c's space
-    int64_t nel = vox(s) * c.cout;
-    __nv_bfloat16* dyb = reinterpret_cast<__nv_bfloat16*>(n->g_c);
-    k_to_bf16<<<nblk(nel), 256, 0, n->s>>>(dY, dyb, nel);
-    if (n->KZ == 3) return conv_launch<3>(n, dyb, s, c.cout, n->wflip, nullptr, 0, nullptr, dX, c.cin, c.ks);
-    return conv_launch<1>(n, dyb, s, c.cout, n->wflip, nullptr, 0, nullptr, dX, c.cin, c.ks);
+    // gradients stay FP32 (staged as FP32 in shared memory)
+    if (n->KZ == 3) return conv_launch<3, float>(n, dY, s, c.cout, n->wflip, nullptr, 0, nullptr, dX, c.cin, c.ks);
+    return conv_launch<1, float>(n, dY, s, c.cout, n->wflip, nullptr, 0, nullptr, dX, c.cin, c.ks);
 }
 
 cudaError_t conv_wgrad(stokes_net_s* n, int li, const __nv_bfloat16* X, Shape s, const float* dY) {

@@ -522,6 +522,7 @@ cudaError_t launch_build_weights(Ctx* c, const double* phiL, const double* phiS,
     cudaStream_t s = c->stream;
     DevArrays D = c->dev_arrays();
     cudaError_t e;
+    cudaGetLastError();   // a stale, non-sticky error from earlier work is not this call's
     // pads and guards must read as zero; coefficients of inactive real
     // unknowns are written below
     if ((e = c->zero_weights()) != cudaSuccess) return e;
