@@ -17,6 +17,15 @@ Concatenation order is [upsampled, skip].  Spatial sizes must be multiples
 of 4.  Convolutions use zero padding 1.  Everything is FP64 torch CPU math;
 torch's convolution routine is the library primitive, gradients come from
 autograd.
+
+``store`` optionally models a network that keeps its activations in a
+narrower type: it is applied to every hidden activation after its ReLU and
+to every pooled map (the values a kernel writes to memory and reads back),
+with the gradient passed straight through, so the result is the FP64
+network evaluated at the stored values.  ``bf16_store`` rounds to bfloat16
+(round to nearest, ties to even).  ReLU masks and weight gradients then see
+the same stored values as a kernel that stores BF16, which is how two
+implementations can take the same ReLU decisions.
 """
 import numpy as np
 import torch
@@ -79,24 +88,31 @@ def _up(x):
     return Fn.interpolate(x, scale_factor=2, mode="nearest")
 
 
-def forward(theta, x, dim, cin, cout):
+def bf16_store(t):
+    """Values rounded to bfloat16, gradient passed through unchanged."""
+    return t + (t.detach().to(torch.bfloat16).to(torch.float64) - t.detach())
+
+
+def forward(theta, x, dim, cin, cout, store=None):
     """x: (B, cin, [Z,] Y, X) float64 tensor -> (B, cout, ...)."""
     P = unpack(theta, dim, cin, cout)
-    r = torch.relu
+    s = store or (lambda t: t)
+    r = lambda t: s(torch.relu(t))
+    pool = lambda t: s(_pool(t, dim))
     e0 = r(_conv(r(_conv(x, P["enc0a"], dim)), P["enc0b"], dim))
-    e1 = r(_conv(r(_conv(_pool(e0, dim), P["enc1a"], dim)), P["enc1b"], dim))
-    e2 = r(_conv(r(_conv(_pool(e1, dim), P["enc2a"], dim)), P["enc2b"], dim))
+    e1 = r(_conv(r(_conv(pool(e0), P["enc1a"], dim)), P["enc1b"], dim))
+    e2 = r(_conv(r(_conv(pool(e1), P["enc2a"], dim)), P["enc2b"], dim))
     d1 = r(_conv(r(_conv(torch.cat([_up(e2), e1], 1), P["dec1a"], dim)), P["dec1b"], dim))
     d0 = r(_conv(r(_conv(torch.cat([_up(d1), e0], 1), P["dec0a"], dim)), P["dec0b"], dim))
     return _conv(d0, P["out"], dim)
 
 
-def loss_and_grad(theta_np, x_np, y_np, dim, cin, cout):
+def loss_and_grad(theta_np, x_np, y_np, dim, cin, cout, store=None):
     """Mean over samples of ||N(x) - y||^2 / ||y||^2 and its gradient."""
     theta = torch.tensor(theta_np, dtype=torch.float64, requires_grad=True)
     x = torch.as_tensor(x_np, dtype=torch.float64)
     y = torch.as_tensor(y_np, dtype=torch.float64)
-    out = forward(theta, x, dim, cin, cout)
+    out = forward(theta, x, dim, cin, cout, store)
     num = ((out - y) ** 2).flatten(1).sum(1)
     den = (y ** 2).flatten(1).sum(1).clamp_min(1e-300)
     loss = (num / den).mean()
@@ -104,7 +120,7 @@ def loss_and_grad(theta_np, x_np, y_np, dim, cin, cout):
     return float(loss), theta.grad.numpy().copy()
 
 
-def predict(theta_np, x_np, dim, cin, cout):
+def predict(theta_np, x_np, dim, cin, cout, store=None):
     with torch.no_grad():
         return forward(torch.as_tensor(theta_np), torch.as_tensor(x_np, dtype=torch.float64), dim, cin,
-                       cout).numpy()
+                       cout, store).numpy()

@@ -1,9 +1,13 @@
 """The CUDA U-Net against the FP64 CPU reference (oracle.unet).
 
-BF16 activations with FP32 accumulation: the forward output must agree with
-the FP64 reference to 2e-2 relative (RMS over the output), and the parameter
-gradient must point the same way (cosine similarity >= 0.999, relative norm
-difference <= 5e-2).  A few Adam steps must reduce the loss."""
+BF16 activations with FP32 accumulation.  Against the FP64 reference that
+stores its activations in BF16 the same way (oracle.unet.bf16_store, so both
+sides take the same ReLU decisions) the forward output must agree to 2e-3
+relative (RMS over the output) and the parameter gradient to a cosine
+similarity >= 0.9999 and a relative norm difference <= 1e-2.  Against the
+plain FP64 network the forward output must agree to 2e-2 and the gradient to
+a cosine >= 0.995 (the rest is the BF16 storage itself).  A few Adam steps
+must reduce the loss."""
 import numpy as np
 import pytest
 
@@ -37,11 +41,13 @@ def test_forward_matches_oracle(dim, cin, cout, shape):
     net, th, x, y, to_nc = _setup(dim, cin, cout, shape, 1)
     # the oracle sees the same BF16-rounded input the network stores
     xb = torch.tensor(x).to(torch.bfloat16).to(torch.float64).numpy()
-    ref = U.predict(net.to_oracle_layout(net.get_params()), to_nc(xb), dim, cin, cout)
+    th32 = net.to_oracle_layout(net.get_params())
     got = net.forward(torch.tensor(x.reshape(-1)).cuda(), shape).cpu().numpy().reshape(y.shape)
     got = np.moveaxis(got, -1, 1)
-    err = np.sqrt(np.mean((got - ref) ** 2)) / np.sqrt(np.mean(ref ** 2))
-    assert err < 2e-2, err
+    for store, tol in ((U.bf16_store, 2e-3), (None, 2e-2)):
+        ref = U.predict(th32, to_nc(xb), dim, cin, cout, store=store)
+        err = np.sqrt(np.mean((got - ref) ** 2)) / np.sqrt(np.mean(ref ** 2))
+        assert err < tol, (store, err)
 
 
 @pytest.mark.parametrize("dim,cin,cout,shape", [(2, 8, 4, (2, 1, 16, 12)), (3, 12, 8, (1, 8, 8, 12))])
@@ -50,13 +56,14 @@ def test_gradient_matches_oracle(dim, cin, cout, shape):
     net, th, x, y, to_nc = _setup(dim, cin, cout, shape, 2)
     xb = torch.tensor(x).to(torch.bfloat16).to(torch.float64).numpy()
     theta = net.to_oracle_layout(net.get_params())
-    L_ref, g_ref = U.loss_and_grad(theta, to_nc(xb), to_nc(y), dim, cin, cout)
     L, g = net.gradient(torch.tensor(x.reshape(-1)).cuda(), torch.tensor(y.reshape(-1)).cuda(), shape)
     g = net.to_oracle_layout(g)
-    assert abs(L - L_ref) <= 2e-2 * abs(L_ref)
-    cos = g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref))
-    assert cos >= 0.999, cos
-    assert abs(np.linalg.norm(g) - np.linalg.norm(g_ref)) <= 5e-2 * np.linalg.norm(g_ref)
+    for store, ltol, ctol, ntol in ((U.bf16_store, 2e-3, 0.9999, 1e-2), (None, 2e-2, 0.995, 5e-2)):
+        L_ref, g_ref = U.loss_and_grad(theta, to_nc(xb), to_nc(y), dim, cin, cout, store=store)
+        assert abs(L - L_ref) <= ltol * abs(L_ref), (store, L, L_ref)
+        cos = g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref))
+        assert cos >= ctol, (store, cos)
+        assert abs(np.linalg.norm(g) - np.linalg.norm(g_ref)) <= ntol * np.linalg.norm(g_ref), store
 
 
 def test_training_reduces_loss():

@@ -67,3 +67,29 @@ def test_gradient_matches_finite_differences(dim):
         e[i] = h
         fd = (U.loss_and_grad(th + e, x, y, dim, cin, cout)[0] - U.loss_and_grad(th - e, x, y, dim, cin, cout)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])) + 1e-8, (i, fd, g[i])
+
+
+def test_bf16_store_rounds_to_nearest_even_and_passes_gradients():
+    # bfloat16 keeps 8 significant bits: the spacing just above 1 is 2^-7
+    vals = torch.tensor([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -8 + 2.0 ** -20, -(1 + 2.0 ** -8 + 2.0 ** -20),
+                         3.0, 0.0], dtype=torch.float64, requires_grad=True)
+    want = [1.0, 1 + 2.0 ** -6, 1 + 2.0 ** -7, -(1 + 2.0 ** -7), 3.0, 0.0]
+    got = U.bf16_store(vals)
+    assert got.detach().tolist() == want
+    w = torch.arange(6, dtype=torch.float64)
+    (got * w).sum().backward()
+    assert vals.grad.tolist() == w.tolist()
+
+
+def test_store_hook_is_neutral_when_it_is_the_identity():
+    rng = np.random.default_rng(11)
+    th = U.init_params(2, 4, 3, seed=2)
+    x = rng.normal(size=(1, 4, 8, 8))
+    y = rng.normal(size=(1, 3, 8, 8))
+    L0, g0 = U.loss_and_grad(th, x, y, 2, 4, 3)
+    L1, g1 = U.loss_and_grad(th, x, y, 2, 4, 3, store=lambda t: t)
+    assert L0 == L1 and np.array_equal(g0, g1)
+    # BF16 storage changes the output by about the BF16 precision, no more
+    a = U.predict(th, x, 2, 4, 3)
+    b = U.predict(th, x, 2, 4, 3, store=U.bf16_store)
+    assert 0 < np.abs(a - b).max() <= 3e-2 * np.abs(a).max()
