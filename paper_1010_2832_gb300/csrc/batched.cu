@@ -577,6 +577,16 @@ stokes_status stokes_batch_create(stokes_batch* out, int n, const stokes_ctx* ct
         e = cudaMemcpyAsync(b->c[i]->b64, b->c[i]->A.minv64, sizeof(double) * b->c[i]->vec_elems(),
                             cudaMemcpyDeviceToDevice, b->s);
     if (e == cudaSuccess) e = autotune(b, tune_cache);
+    // the tuning runs may have covered slots (inactive ones in coarser tiles)
+    // that the chosen work list never initialises: clear every vector they
+    // wrote, so the unpacked solution is zero on inactive unknowns
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        Ctx* c = b->c[i];
+        const size_t bytes = sizeof(double) * c->vec_elems();
+        double* vs[] = {c->x64, c->b64, c->w64.r, c->w64.z, c->w64.q, c->w64.p[0], c->w64.p[1]};
+        for (double* v : vs)
+            if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, bytes, b->s);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
     if (e != cudaSuccess) {
         if (std::getenv("STOKES_VERBOSE")) std::fprintf(stderr, "stokes_batch_create: %s\n", cudaGetErrorString(e));
