@@ -227,11 +227,13 @@ __global__ void __launch_bounds__(256) k_sw_finish(Layout L, const int* __restri
     schwarz_gather_slot(L, D, P, w.r, w.z, c0 + (threadIdx.x & 31), r0 + (threadIdx.x >> 5), rz, rr);
     block_partial2(warp_sum(rz), warp_sum(rr), partial, counter, nblocks, [&](double trz, double trr) {
         if (INIT) {
+            const bool timed_out = sc->status == STOKES_ERR_TIMEOUT;   // set by a local solve
             sc->rz = trz; sc->rr = trr; sc->rr0 = trr;
             sc->tol2 = sc->tol_rel * sc->tol_rel * trr;
             sc->beta = 0.0; sc->iter = 0; sc->status = 0;
             sc->done = (trr <= sc->tol2 || trr == 0.0) ? 1 : 0;
             if (!isfinite(trr)) { sc->done = 1; sc->status = STOKES_ERR_NONFINITE; }
+            if (timed_out) { sc->done = 1; sc->status = STOKES_ERR_TIMEOUT; }
         } else {
             sc->rr = trr;
             sc->iter += 1;
@@ -278,17 +280,24 @@ static cudaError_t schwarz_build(Ctx* c) {
     if ((e = al((void**)&P.corner, sizeof(int) * np)) != cudaSuccess) return e;
     if ((e = al((void**)&P.nloc, sizeof(int) * np)) != cudaSuccess) return e;
     if ((e = al((void**)&P.lmap, sizeof(short) * np * PMAX)) != cudaSuccess) return e;
-    if ((e = al((void**)&P.inv, sizeof(__nv_bfloat16) * np * PMAX * PMAX)) != cudaSuccess) return e;
-    if ((e = al((void**)&P.ybuf, sizeof(float) * np * PMAX)) != cudaSuccess) return e;
+    // FP32 factors: BF16 storage halves the local-solve traffic but, measured
+    // on the 1024^2 bump workload, needs 4.4x the CG iterations
+    P.xbf16 = 0;
+    if ((e = al((void**)&P.inv, (P.xbf16 ? 2 : 4) * np * PFAC)) != cudaSuccess) return e;
+    if ((e = al((void**)&P.scale, sizeof(float) * np * PMAX)) != cudaSuccess) return e;
+    if ((e = al((void**)&P.ybuf, sizeof(float) * ng * PMAX)) != cudaSuccess) return e;
     cudaMemcpyAsync(P.pid, pid.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, c->stream);
     if (P.np) cudaMemcpyAsync(P.corner, corner.data(), sizeof(int) * P.np, cudaMemcpyHostToDevice, c->stream);
-    cudaMemsetAsync(P.ybuf, 0, sizeof(float) * np * PMAX, c->stream);
-    const int smem = (2 * PMAX * PMAX + PMAX) * (int)sizeof(float);
+    cudaMemsetAsync(P.ybuf, 0, sizeof(float) * ng * PMAX, c->stream);
+    const int smem = SW_SETUP_SMEM;
     cudaFuncSetAttribute(k_schwarz_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_schwarz_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sw_gemv_smem<float>());
+    cudaFuncSetAttribute(k_schwarz_gemv<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         sw_gemv_smem<__nv_bfloat16>());
     cudaEvent_t a, b;
     cudaEventCreate(&a); cudaEventCreate(&b);
     cudaEventRecord(a, c->stream);
-    if (P.np) k_schwarz_setup<<<P.np, 256, smem, c->stream>>>(L, c->A, c->A.coef32, P);
+    if (P.np) k_schwarz_setup<<<P.np, 256, smem, c->stream>>>(L, c->A, c->A.coef64, P);
     cudaEventRecord(b, c->stream);
     if ((e = cudaEventSynchronize(b)) != cudaSuccess) return e;
     float ms = 0;
@@ -311,7 +320,7 @@ static void schwarz_body(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, i
     a.sc = c->sc;
     launch_apply_mode<float, float>(L, c->tiles, nb, c->coef<float>(), w.z, w.q, MODE_CG, a, s);
     k_cg_xr<<<nb, 256, 0, s>>>(L, c->tiles, c->nf, w, w.p[parity ^ 1], c->sc);
-    if (c->sw->np) k_schwarz_gemv<<<c->sw->np, 128, 0, s>>>(L, *c->sw, w.r, c->sc);
+    launch_schwarz_gemv(L, *c->sw, w.r, c->sc, s);
     k_sw_finish<0><<<nb, 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc, c->partial, c->counter, nb, h, use_cond);
 }
 
@@ -320,7 +329,7 @@ static void schwarz_start(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, 
     const int nb = c->ntiles_active;
     CgWork<float>& w = c->w32;
     k_sw_init<<<nb, 256, 0, s>>>(L, c->tiles, c->w64.r, w, c->sc);
-    if (c->sw->np) k_schwarz_gemv<<<c->sw->np, 128, 0, s>>>(L, *c->sw, w.r, c->sc);
+    launch_schwarz_gemv(L, *c->sw, w.r, c->sc, s);
     k_sw_finish<1><<<nb, 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc, c->partial, c->counter, nb, h, use_cond);
 }
 
@@ -617,6 +626,7 @@ stokes_status solve_system(Ctx* c, const double* b, double* x, const stokes_opti
         if (std::getenv("STOKES_VERBOSE"))
             std::fprintf(stderr, "[stokes] outer %d mode %d precond %d inner iters %d status %d rel %.3e -> %.3e\n",
                          outer, mode, o->precond, c->h_sc[0].iter, ist, std::sqrt(rr / bb), std::sqrt(rr_new / bb));
+        if (ist == STOKES_ERR_TIMEOUT) { status = ist; break; }   // a bounded device wait ran out
         if (!(rr_new <= 4.0 * rr) || !std::isfinite(rr_new)) {
             // the step made the FP64 residual grow (refinement diverging at
             // this inner precision): undo it and move the inner solve up one
@@ -673,9 +683,11 @@ cudaError_t apply_preconditioner(Ctx* c, int which, const float* r, float* z) {
     w.r = (float*)r;
     w.z = z;
     const int nb = c->ntiles_active;
-    if (c->sw->np) k_schwarz_gemv<<<c->sw->np, 128, 0, s>>>(L, *c->sw, r, c->sc);
+    launch_schwarz_gemv(L, *c->sw, r, c->sc, s);
     if (nb) k_sw_finish<1><<<nb, 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc, c->partial, c->counter, nb, 0, 0);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = fetch_scalars(c)) != cudaSuccess) return e;
+    return c->h_sc[0].status == STOKES_ERR_TIMEOUT ? cudaErrorLaunchTimeout : cudaSuccess;
 }
 
 double schwarz_setup_ms(Ctx* c) { return c->sw_ready ? c->sw_setup_ms : -1.0; }

@@ -13,12 +13,21 @@
 //   2. assemble A_p from the operator coefficients, C on the stress diagonal
 //      plus K_f beta_f beta_f^T for every face touching the patch, faces in a
 //      fixed order (the local matrices are reproducible bit for bit);
-//   3. scale to unit diagonal, Cholesky, solve for the inverse column by
-//      column, scale back, store in BF16.
-// Apply (every CG step): one CTA per patch computes y_p = A_p^-1 r_p (FP32
-// accumulation); a gather kernel sums, for every unknown, the contributions
-// of the (at most four) patches covering it in a fixed order, so the
-// preconditioner is symmetric and deterministic.  Inactive unknowns get z = r.
+//   3. rotate every cell's (tau_xx, p) pair to (tau_xx + p, tau_xx - p)/sqrt2
+//      (u faces couple only tau_xx - p, v faces only tau_xx + p, so a cell
+//      whose faces in one direction are nearly dead has one combination
+//      held only by the tiny stress block C: in the original basis that is
+//      an eigenvalue near 1e-8 after diagonal scaling, which FP32 cannot
+//      factor; after the rotation the diagonal scaling absorbs it);
+//   4. scale to unit diagonal (D^-1/2 Q A_p Q D^-1/2 = L L^T), Cholesky, invert
+//      the factor (X = L^-1) and store it in FP32 (BF16 loses the small-
+//      eigenvalue directions of the worst-conditioned patches, and those
+//      then cost many CG iterations on large grids).
+// Apply (every CG step): one warp per patch computes
+// z_p = D^-1/2 X^T X D^-1/2 r_p (FP32 accumulation), symmetric positive
+// definite whatever the rounding of X; a gather kernel sums, for every
+// unknown, the contributions of the (at most four) patches covering it in a
+// fixed order, so the preconditioner is symmetric and deterministic.  Inactive unknowns get z = r.
 #include <cmath>
 #include <vector>
 #include "internal.cuh"
@@ -29,6 +38,11 @@ namespace stk {
 constexpr int PB = 4;               // patch core (slots per side)
 constexpr int PR = PB + 2;          // with the one-slot ring
 constexpr int PMAX = 3 * PR * PR;   // unknowns per patch at most (2D: 108)
+// Packed lower triangle with every row padded to a multiple of 4 entries, so
+// rows start on 16-byte boundaries: row r (group m = r / 4, rows of group m
+// hold 4(m+1) entries) starts at 8 m (m+1) + (r - 4m) 4 (m+1).
+__host__ __device__ constexpr int tri4_off(int r) { return 8 * (r / 4) * (r / 4 + 1) + (r - 4 * (r / 4)) * 4 * (r / 4 + 1); }
+constexpr int PFAC = tri4_off(PMAX);                          // 6048 floats per patch
 
 struct SchwarzPlan {
     int npx, npy;                   // patch grid over slots [0, nx] x [0, ny]
@@ -36,8 +50,12 @@ struct SchwarzPlan {
     int* corner;                    // [np] packed (I, J)
     int* nloc;                      // [np] active unknowns per patch
     short* lmap;                    // [np * PMAX] local index of (f, jj, ii) or -1
-    __nv_bfloat16* inv;             // [np * PMAX * PMAX] local inverses
-    float* ybuf;                    // [np * PMAX]
+    void* inv;                      // [np * PFAC] X = L^-1 of each scaled patch matrix, padded packed
+                                    // rows, FP32 or (xbf16) BF16
+    int xbf16;
+    float* scale;                   // [np * PMAX] D^-1/2 of each patch, by position (f, jj, ii)
+    float* ybuf;                    // [npy * npx * PMAX] local results by grid patch and position
+                                    // (f, jj, ii); zero for inactive patches and positions
     int np;
 };
 
@@ -58,13 +76,19 @@ __global__ void k_schwarz_mark(Layout L, DevArrays D, int npx, int npy, int* fla
     flag[J * npx + I] = any;
 }
 
-// one CTA (256 threads) per active patch; dynamic smem: A (PMAX^2 floats),
-// X (PMAX^2 floats), diag scale, map
-__global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, const float* coef, SchwarzPlan P) {
-    extern __shared__ __align__(16) float sm[];
-    float* A = sm;                       // n x n (row-major, stride PMAX)
-    float* X = A + PMAX * PMAX;          // inverse columns
-    float* sc = X + PMAX * PMAX;         // 1/sqrt(diag)
+// one CTA (256 threads) per active patch.  The local matrix is assembled in
+// FP64 from the FP64 operator coefficients: in FP32 the cancellation between
+// face terms leaves some patch matrices indefinite.  Only the unit-diagonal
+// matrix is rounded to FP32 for the factorisation.  Dynamic smem: the FP64
+// matrix (PMAX^2 doubles, later reused for X), the scaled FP32 matrix
+// (PMAX^2 floats), the diagonal scaling.
+constexpr int SW_SETUP_SMEM = PMAX * PMAX * 8 + PMAX * PMAX * 4 + PMAX * 4;
+__global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, const double* coef, SchwarzPlan P) {
+    extern __shared__ __align__(16) double smd[];
+    double* Ad = smd;                                        // n x n (row-major, stride PMAX), FP64
+    float* A = reinterpret_cast<float*>(smd + PMAX * PMAX);  // scaled copy, FP32
+    float* sc = A + PMAX * PMAX;                             // 1/sqrt(diag)
+    float* X = reinterpret_cast<float*>(smd);                // L^-1, once Ad is no longer needed
     __shared__ short map[PMAX];
     __shared__ int n_s;
     const int p = blockIdx.x;
@@ -72,8 +96,8 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
     const int a0 = PB * I - 1, b0 = PB * J - 1;       // ring origin (slot coords)
     const int t = threadIdx.x;
     const int64_t S = L.stride;
-    const float *a_c = coef, *a_n = coef + S, *d_c = coef + 2 * S, *d_n = coef + 3 * S, *K_u = coef + 4 * S,
-                *K_v = coef + 5 * S;
+    const double *a_c = coef, *a_n = coef + S, *d_c = coef + 2 * S, *d_n = coef + 3 * S, *K_u = coef + 4 * S,
+                 *K_v = coef + 5 * S;
     // 1. local indices in fixed order (thread 0: 108 positions)
     if (t == 0) {
         int n = 0;
@@ -89,7 +113,7 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
     __syncthreads();
     const int n = n_s;
     for (int e = t; e < PMAX; e += 256) P.lmap[(int64_t)p * PMAX + e] = map[e];
-    for (int e = t; e < n * PMAX; e += 256) A[e] = 0.f;
+    for (int e = t; e < n * PMAX; e += 256) Ad[e] = 0.0;
     __syncthreads();
     auto lidx = [&](int f, int i, int j) -> int {
         int ii = i - a0, jj = j - b0;
@@ -102,7 +126,7 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
         int k = map[(f * PR + jj) * PR + ii];
         if (k >= 0) {
             int64_t o = L.off(a0 + ii + 1, b0 + jj + 1, 0);
-            A[k * PMAX + k] += (f == 0 ? d_c : d_n)[o];
+            Ad[k * PMAX + k] += (f == 0 ? d_c : d_n)[o];
         }
     }
     __syncthreads();
@@ -118,12 +142,12 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
                                          : (i >= 0 && i < L.nx && j >= 0 && j <= L.ny);
                     if (!ku_ok) continue;
                     int64_t o = L.off(i + 1, j + 1, 0);
-                    float K = (dir == 0 ? K_u : K_v)[o];
-                    if (K == 0.f) continue;
+                    double K = (dir == 0 ? K_u : K_v)[o];
+                    if (K == 0.0) continue;
                     int idx[6];
-                    float b[6];
+                    double b[6];
                     if (dir == 0) {
-                        float am = a_c[L.off(i, j + 1, 0)], ap = a_c[o];
+                        double am = a_c[L.off(i, j + 1, 0)], ap = a_c[o];
                         idx[0] = lidx(0, i - 1, j); b[0] = am;       // txx(i-1): +a
                         idx[1] = lidx(2, i - 1, j); b[1] = -am;      // p(i-1):   -a
                         idx[2] = lidx(0, i, j);     b[2] = -ap;      // txx(i):   -a
@@ -131,7 +155,7 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
                         idx[4] = lidx(1, i, j);     b[4] = a_n[o];                     // txy(i, j)
                         idx[5] = lidx(1, i, j + 1); b[5] = -a_n[L.off(i + 1, j + 2, 0)];  // txy(i, j+1)
                     } else {
-                        float am = a_c[L.off(i + 1, j, 0)], ap = a_c[o];
+                        double am = a_c[L.off(i + 1, j, 0)], ap = a_c[o];
                         idx[0] = lidx(0, i, j - 1); b[0] = -am;      // txx(j-1): -a
                         idx[1] = lidx(2, i, j - 1); b[1] = -am;      // p(j-1):   -a
                         idx[2] = lidx(0, i, j);     b[2] = ap;       // txx(j):   +a
@@ -141,19 +165,45 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
                     }
                     for (int q = t; q < 36; q += 32) {
                         int r = q / 6, c = q % 6;
-                        if (idx[r] >= 0 && idx[c] >= 0) A[idx[r] * PMAX + idx[c]] += K * b[r] * b[c];
+                        if (idx[r] >= 0 && idx[c] >= 0) Ad[idx[r] * PMAX + idx[c]] += K * b[r] * b[c];
                     }
                     __syncwarp();
                 }
         }
     }
     __syncthreads();
-    // 3. unit-diagonal scaling, Cholesky (lower, in place), inverse
-    for (int k = t; k < n; k += 256) sc[k] = A[k * PMAX + k] > 0.f ? rsqrtf(A[k * PMAX + k]) : 1.f;
+    // 3. Q A_p Q with Q the symmetric orthogonal pair rotation (rows, then columns)
+    constexpr double H = 0.70710678118654752440;
+    for (int e = t; e < PR * PR * n; e += 256) {
+        int cell = e / n, c = e % n;
+        int kt = map[cell], kp = map[2 * PR * PR + cell];
+        if (kt < 0 || kp < 0) continue;
+        double a = Ad[kt * PMAX + c], b = Ad[kp * PMAX + c];
+        Ad[kt * PMAX + c] = (a + b) * H;
+        Ad[kp * PMAX + c] = (a - b) * H;
+    }
+    __syncthreads();
+    for (int e = t; e < PR * PR * n; e += 256) {
+        int cell = e / n, r = e % n;
+        int kt = map[cell], kp = map[2 * PR * PR + cell];
+        if (kt < 0 || kp < 0) continue;
+        double a = Ad[r * PMAX + kt], b = Ad[r * PMAX + kp];
+        Ad[r * PMAX + kt] = (a + b) * H;
+        Ad[r * PMAX + kp] = (a - b) * H;
+    }
+    __syncthreads();
+    // 4. unit-diagonal scaling (FP64, then rounded), Cholesky (lower, in
+    // place, FP32), inverse of the factor
+    for (int k = t; k < n; k += 256) {
+        double d = Ad[k * PMAX + k];
+        sc[k] = d > 0.0 ? (float)(1.0 / sqrt(d)) : 1.f;
+    }
     __syncthreads();
     for (int e = t; e < n * n; e += 256) {
         int r = e / n, c = e % n;
-        A[r * PMAX + c] *= sc[r] * sc[c];
+        double dr = Ad[r * PMAX + r], dc = Ad[c * PMAX + c];
+        double v = Ad[r * PMAX + c];
+        A[r * PMAX + c] = (dr > 0.0 && dc > 0.0) ? (float)(v / sqrt(dr * dc)) : (r == c ? 1.f : 0.f);
     }
     __syncthreads();
     for (int k = 0; k < n; ++k) {
@@ -172,88 +222,256 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
         }
         __syncthreads();
     }
-    // column c of the inverse: L y = e_c, L^T x = y (thread c, column in X)
+    // X = L^-1, column c by thread c (forward substitution on e_c)
     for (int c = t; c < n; c += 256) {
-        for (int r = 0; r < n; ++r) X[r * PMAX + c] = 0.f;
         for (int r = c; r < n; ++r) {
             float s = r == c ? 1.f : 0.f;
             for (int q = c; q < r; ++q) s -= A[r * PMAX + q] * X[q * PMAX + c];
             X[r * PMAX + c] = s / A[r * PMAX + r];
         }
-        for (int r = n - 1; r >= 0; --r) {
-            float s = X[r * PMAX + c];
-            for (int q = r + 1; q < n; ++q) s -= A[q * PMAX + r] * X[q * PMAX + c];
-            X[r * PMAX + c] = s / A[r * PMAX + r];
-        }
     }
     __syncthreads();
-    __nv_bfloat16* out = P.inv + (int64_t)p * PMAX * PMAX;
-    for (int e = t; e < n * n; e += 256) {
-        int r = e / n, c = e % n;
-        out[e] = __float2bfloat16(X[r * PMAX + c] * sc[r] * sc[c]);
+    // packed rows of X (row r: X[r][0..r]) and the scaling.  The patch
+    // operator D^-1/2 X^T X D^-1/2 is symmetric positive definite whatever
+    // the rounding of X (X stays triangular with a positive diagonal).
+    const int n4 = (n + 3) / 4 * 4;
+    for (int e = t; e < n * n4; e += 256) {
+        int r = e / n4, c = e % n4;
+        if (c < (r / 4 + 1) * 4) {
+            const float v = c <= r ? X[r * PMAX + c] : 0.f;
+            const int64_t at = (int64_t)p * PFAC + tri4_off(r) + c;
+            if (P.xbf16) static_cast<__nv_bfloat16*>(P.inv)[at] = __float2bfloat16(v);
+            else static_cast<float*>(P.inv)[at] = v;
+        }
     }
+    for (int e = t; e < PMAX; e += 256) P.scale[(int64_t)p * PMAX + e] = map[e] >= 0 ? sc[map[e]] : 0.f;
 }
 
-// y_p = A_p^-1 r_p, one CTA (128 threads) per patch; a warp per row
+// Shared-memory address of a pointer (for mbarrier and bulk-copy operands).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Polls of the bulk copy's mbarrier before a local solve gives up (each
+// try_wait itself blocks for a while); the copy of 23 KB takes microseconds.
+constexpr long long SW_WAIT_POLLS = 1LL << 22;
+
+// Wait for phase `parity` of an mbarrier, at most SW_WAIT_POLLS polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long long i = 0; i < SW_WAIT_POLLS; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Bytes of patch p's packed factor (a multiple of 16).
+template <class T>
+__device__ __forceinline__ uint32_t sw_bytes(const SchwarzPlan& P, int p) {
+    return (uint32_t)((tri4_off(P.nloc[p]) * (int)sizeof(T) + 15) / 16 * 16);
+}
+
+// four consecutive stored entries as floats (16-byte or 8-byte loads)
+__device__ __forceinline__ float4 ld4(const float* x) { return *reinterpret_cast<const float4*>(x); }
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16* x) {
+    const uint2 u = *reinterpret_cast<const uint2*>(x);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Start the bulk (TMA) copy of one packed factor into shared memory,
+// completing on mbarrier `bar` (one thread).
+__device__ __forceinline__ void sw_issue(uint32_t bar, void* dst, const void* src, uint32_t bytes) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    if (bytes > 0)
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(dst)),
+                     "l"(src), "r"(bytes), "r"(bar)
+                     : "memory");
+}
+
+// z_p = Q D^-1/2 X^T X D^-1/2 Q r_p with X = L^-1, one CTA (128 threads)
+// per active patch.  Thread 0 starts a bulk (TMA) copy of the packed factor
+// into shared memory, completing on an mbarrier; meanwhile the threads
+// gather, rotate and scale r_p into s.  Then y = X s (thread t: row t,
+// 16-byte loads of the padded rows) and z = X^T y (four threads per block of
+// four columns, each taking every fourth row, joined by shuffles); rotate
+// back and store by position.  About 25 KB of shared memory per CTA, so
+// eight CTAs share an SM and their copies overlap each other's arithmetic.
+// A copy that never completes (bounded wait) marks the solve
+// STOKES_ERR_TIMEOUT and ends it.
+template <class T>
 __global__ void __launch_bounds__(128) k_schwarz_gemv(Layout L, SchwarzPlan P, const float* __restrict__ r,
-                                                      const CgScalars* sc) {
-    __shared__ float rp[PMAX];
+                                                      CgScalars* sc) {
+    extern __shared__ __align__(128) unsigned char xs_raw[];   // PFAC entries of T
+    T* Xs = reinterpret_cast<T*>(xs_raw);
+    __shared__ __align__(16) float s[PMAX];
+    __shared__ float y[PMAX];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int ok_s;
     if (sc->done) return;
+    const int t = threadIdx.x;
     const int p = blockIdx.x;
+    const uint32_t b_addr = smem_u32(&bar);
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_addr), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sw_issue(b_addr, Xs, static_cast<const T*>(P.inv) + (int64_t)p * PFAC, sw_bytes<T>(P, p));
+    }
+    constexpr float H = 0.70710678118654752f;
     const int n = P.nloc[p];
     const int I = P.corner[p] & 0xffff, J = P.corner[p] >> 16;
     const int a0 = PB * I - 1, b0 = PB * J - 1;
     const short* map = P.lmap + (int64_t)p * PMAX;
-    for (int e = threadIdx.x; e < PMAX; e += 128) {
-        int k = map[e];
-        if (k >= 0) {
-            int f = e / (PR * PR), rem = e % (PR * PR), jj = rem / PR, ii = rem % PR;
-            rp[k] = r[(int64_t)f * L.stride + L.off(a0 + ii + 1, b0 + jj + 1, 0)];
+    const float* scl = P.scale + (int64_t)p * PMAX;
+    // gather, rotate and scale: position e < PR^2 handles the cell's
+    // (tau_xx, p) pair, e in [PR^2, 2 PR^2) the node's tau_xy.  All loads
+    // are independent (r is zero on inactive unknowns and outside the grid,
+    // the scaling is stored by position), so they are in flight together.
+    int kk = -1, kp = -1;
+    float sa = 0.f, sb = 0.f;
+    if (t < 2 * PR * PR) {
+        const int e = t;
+        const int rem = e % (PR * PR), jj = rem / PR, ii = rem % PR;
+        const int64_t o = L.off(a0 + ii + 1, b0 + jj + 1, 0);
+        kk = map[e];
+        sa = scl[e];
+        if (e >= PR * PR) {
+            const float rv = r[L.stride + o];
+            if (kk >= 0) s[kk] = rv * sa;
+        } else {
+            kp = map[2 * PR * PR + e];
+            sb = scl[2 * PR * PR + e];
+            const float rt = r[o], rp = r[2 * L.stride + o];
+            // the scaling belongs to the rotated unknowns: rotate, then scale
+            if (kk >= 0 && kp >= 0) {
+                s[kk] = (rt + rp) * H * sa;
+                s[kp] = (rt - rp) * H * sb;
+            } else if (kk >= 0) {
+                s[kk] = rt * sa;
+            } else if (kp >= 0) {
+                s[kp] = rp * sb;
+            }
         }
     }
+    if (t >= n && t < (n + 3) / 4 * 4) s[t] = 0.f;    // the padded last block
+    if (t == 0) ok_s = mbar_wait(b_addr, 0) ? 1 : 0;
     __syncthreads();
-    const __nv_bfloat16* M = P.inv + (int64_t)p * PMAX * PMAX;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int row = w; row < n; row += 4) {
-        float s = 0.f;
-        for (int c = lane; c < n; c += 32) s = fmaf(__bfloat162float(M[row * n + c]), rp[c], s);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) P.ybuf[(int64_t)p * PMAX + row] = s;
+    if (!ok_s) {
+        // give the copy one more bounded wait before the CTA leaves
+        if (t == 0) {
+            mbar_wait(b_addr, 0);
+            sc->status = STOKES_ERR_TIMEOUT;
+            sc->done = 1;
+        }
+        return;
+    }
+    const T* X = Xs;
+    if (t < n) {
+        const T* xr = X + tri4_off(t);
+        const float4* s4 = reinterpret_cast<const float4*>(s);
+        float acc = 0.f;
+        for (int j = 0; j <= t / 4; ++j) {
+            const float4 a = ld4(xr + 4 * j), b = s4[j];
+            acc = fmaf(a.x, b.x, acc);
+            acc = fmaf(a.y, b.y, acc);
+            acc = fmaf(a.z, b.z, acc);
+            acc = fmaf(a.w, b.w, acc);
+        }
+        y[t] = acc;
+    }
+    __syncthreads();
+    // z = X^T y: column block cb = t / 4 (columns 4cb..4cb+3), rows
+    // r = 4cb + (t % 4) + 4i; the four partial sums meet by shuffles
+    {
+        const int cb = t >> 2, q = t & 3;
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (4 * cb < n)
+            for (int row = 4 * cb + q; row < n; row += 4) {
+                const float4 a = ld4(X + tri4_off(row) + 4 * cb);
+                const float yr = y[row];
+                z.x = fmaf(a.x, yr, z.x);
+                z.y = fmaf(a.y, yr, z.y);
+                z.z = fmaf(a.z, yr, z.z);
+                z.w = fmaf(a.w, yr, z.w);
+            }
+        for (int o = 1; o <= 2; o <<= 1) {
+            z.x += __shfl_xor_sync(0xffffffffu, z.x, o);
+            z.y += __shfl_xor_sync(0xffffffffu, z.y, o);
+            z.z += __shfl_xor_sync(0xffffffffu, z.z, o);
+            z.w += __shfl_xor_sync(0xffffffffu, z.w, o);
+        }
+        // s is no longer read (y = X s ended at the barrier above)
+        if (q == 0 && 4 * cb < n) reinterpret_cast<float4*>(s)[cb] = z;
+    }
+    __syncthreads();
+    // scale, rotate back and store by position
+    float* out = P.ybuf + (int64_t)(J * P.npx + I) * PMAX;
+    if (t < 2 * PR * PR) {
+        const int e = t;
+        if (e >= PR * PR) {
+            if (kk >= 0) out[e] = s[kk] * sa;
+        } else if (kk >= 0 && kp >= 0) {
+            const float a = s[kk] * sa, b = s[kp] * sb;     // scale, then rotate back
+            out[e] = (a + b) * H;
+            out[2 * PR * PR + e] = (a - b) * H;
+        } else if (kk >= 0) {
+            out[e] = s[kk] * sa;
+        } else if (kp >= 0) {
+            out[2 * PR * PR + e] = s[kp] * sb;
+        }
     }
 }
 
-// z = sum over covering patches (fixed order) for active unknowns, z = r on
-// inactive ones.  Returns this thread's (r.z, r.r) over the slot's fields.
+// dynamic shared memory of k_schwarz_gemv<T>: the packed factor
+template <class T> constexpr int sw_gemv_smem() { return PFAC * (int)sizeof(T); }
+
+static inline void launch_schwarz_gemv(const Layout& L, const SchwarzPlan& P, const float* r, CgScalars* sc,
+                                       cudaStream_t s) {
+    if (!P.np) return;
+    if (P.xbf16) k_schwarz_gemv<__nv_bfloat16><<<P.np, 128, sw_gemv_smem<__nv_bfloat16>(), s>>>(L, P, r, sc);
+    else k_schwarz_gemv<float><<<P.np, 128, sw_gemv_smem<float>(), s>>>(L, P, r, sc);
+}
+
 __device__ __forceinline__ void schwarz_gather_slot(const Layout& L, const DevArrays& D, const SchwarzPlan& P,
                                                     const float* __restrict__ r, float* __restrict__ z, int c,
                                                     int rr, double& rz, double& r2) {
     const int i = c - 1, j = rr - 1;
     const int64_t o = L.off(c, rr, 0);
+    // patch I's ring covers slots [PB I - 1, PB I + PB]:
+    // I from ceil(i / PB) - 1 to floor((i + 1) / PB)   (i >= 0)
+    const int ilo = max((i + PB - 1) / PB - 1, 0), ihi = min((i + 1) / PB, P.npx - 1);
+    const int jlo = max((j + PB - 1) / PB - 1, 0), jhi = min((j + 1) / PB, P.npy - 1);
+    const bool real = i >= 0 && j >= 0 && i <= L.nx && j <= L.ny;
+    // every load is independent: the local results are zero for inactive
+    // patches and for inactive unknowns, so they are summed unconditionally
+    float rv[3], sum[3];
+    bool act[3];
+#pragma unroll
     for (int f = 0; f < 3; ++f) {
-        const int64_t of = (int64_t)f * L.stride + o;
-        const float rv = r[of];
-        float zv;
-        if (!unknown_active(D, L, f, i, j)) {
-            zv = (i >= 0 && j >= 0 && i <= L.nx && j <= L.ny) ? rv : 0.f;
-        } else {
-            float s = 0.f;
-            // patch I's ring covers slots [PB I - 1, PB I + PB]:
-            // I from ceil(i / PB) - 1 to floor((i + 1) / PB)   (i >= 0)
-            const int ilo = (i + PB - 1) / PB - 1, ihi = (i + 1) / PB;
-            const int jlo = (j + PB - 1) / PB - 1, jhi = (j + 1) / PB;
-            for (int J = max(jlo, 0); J <= min(jhi, P.npy - 1); ++J)
-                for (int I = max(ilo, 0); I <= min(ihi, P.npx - 1); ++I) {
-                    const int q = P.pid[J * P.npx + I];
-                    if (q < 0) continue;
-                    const int ii = i - (PB * I - 1), jj = j - (PB * J - 1);
-                    const int k = P.lmap[(int64_t)q * PMAX + (f * PR + jj) * PR + ii];
-                    if (k >= 0) s += P.ybuf[(int64_t)q * PMAX + k];
-                }
-            zv = s;
-        }
-        z[of] = zv;
-        rz += (double)rv * zv;
-        r2 += (double)rv * rv;
+        rv[f] = r[(int64_t)f * L.stride + o];
+        act[f] = unknown_active(D, L, f, i, j);
+        float s = 0.f;
+        for (int J = jlo; J <= jhi; ++J)
+            for (int I = ilo; I <= ihi; ++I) {
+                const int ii = i - (PB * I - 1), jj = j - (PB * J - 1);
+                s += P.ybuf[(int64_t)(J * P.npx + I) * PMAX + (f * PR + jj) * PR + ii];
+            }
+        sum[f] = s;
+    }
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        const float zv = act[f] ? sum[f] : (real ? rv[f] : 0.f);
+        z[(int64_t)f * L.stride + o] = zv;
+        rz += (double)rv[f] * zv;
+        r2 += (double)rv[f] * rv[f];
     }
 }
 

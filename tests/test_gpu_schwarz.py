@@ -1,10 +1,14 @@
 """Additive Schwarz preconditioner (2D) against its definition written out
 in the oracle (dense FP64 local solves), and solves with it.
 
-The GPU stores the local inverses in BF16 (8-bit mantissa) and accumulates in
-FP32, so the preconditioned vector agrees with the FP64 definition to about
-1e-2 relative (RMS); the solve itself is still judged by the FP64 true
-residual."""
+The GPU assembles each local matrix in FP64, factors the unit-diagonal
+matrix in FP32, stores the inverse X = L^-1 of the factor in FP32 and
+applies D^-1/2 X^T X D^-1/2 with FP32 accumulation, so the preconditioned
+vector agrees with the FP64 definition to about 1e-2 relative (RMS; the
+error concentrates in the worst-conditioned patches) while the
+preconditioner stays symmetric positive definite (checked on random
+vectors).  The solve is judged by the FP64 true residual; it must stay in
+FP32 (no precision escalation) and take far fewer iterations than Jacobi."""
 import numpy as np
 import pytest
 
@@ -37,6 +41,19 @@ def test_schwarz_matches_definition(name):
     err = np.sqrt(np.mean((z - z_ref)[act] ** 2)) / np.sqrt(np.mean(z_ref[act] ** 2))
     assert err < 1.5e-2, err
     assert np.array_equal(z[~act], r[~act].astype(np.float32).astype(np.float64))
+    # symmetric positive definite on the active unknowns
+    vs, zs_ = [], []
+    for q in range(4):
+        v = rng.normal(size=S.A.shape[0]) * act
+        zq = ctx.new_vector(torch.float32)
+        ctx.apply_preconditioner(2, ctx.fields_to_slots(torch.from_numpy(v).cuda()).to(torch.float32), zq)
+        vs.append(v)
+        zs_.append(ctx.slots_to_fields(zq.to(torch.float64)).cpu().numpy())
+    for a in range(4):
+        assert vs[a] @ zs_[a] > 0
+        for b in range(a):
+            scale = np.linalg.norm(vs[a]) * np.linalg.norm(zs_[b]) + np.linalg.norm(vs[b]) * np.linalg.norm(zs_[a])
+            assert abs(vs[a] @ zs_[b] - vs[b] @ zs_[a]) <= 1e-5 * scale
 
 
 @pytest.mark.parametrize("name", ["bumps40", "rand37x23"])
@@ -51,7 +68,8 @@ def test_schwarz_solve_reaches_fp64_residual_with_fewer_iterations(name):
     assert st_s["status"] == 0, st_s
     x = torch.cat(out[1] + [out[2]]).cpu().numpy()
     assert So.relative_residual(S.A, x, S.b) <= 1.01e-8
-    assert st_s["iterations"] < st_j["iterations"], (st_s, st_j)
+    assert st_s["precision_used"] == stokes.FP32, st_s
+    assert 3 * st_s["iterations"] < st_j["iterations"], (st_s, st_j)
     x_ref = So.solve_direct(S.A, S.b, S_.pressure_null_vectors(S))
     u_ref = S_.recover_velocity(S, x_ref)
     u = torch.cat([a.reshape(-1) for a in out[0]]).cpu().numpy()
