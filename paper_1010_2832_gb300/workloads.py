@@ -176,17 +176,27 @@ def batch_instances(count=64, n_lo=64, n_hi=512, seed0=4000):
     return out
 
 
-def column_3d(n=256):
+def column_3d(n=256, window=None):
     """3D unit cube: liquid column of radius 0.05 around x = z = 0.5 below
     y = 0.6, standing on a solid floor y < 0.1 (plus walls); rho = 1000,
-    mu = 10, dt = 1e-3; u* = (0, -0.5 - 9.81 dt, 0); static solids."""
+    mu = 10, dt = 1e-3; u* = (0, -0.5 - 9.81 dt, 0); static solids.
+
+    ``window=(i0, j0, k0, ni, nj, nk)`` samples the same fields on the
+    sub-grid of cells [i0, i0+ni) x [j0, j0+nj) x [k0, k0+nk) of the n^3 grid
+    (same spacing and physical positions; the window's own boundary is a
+    wall, so it reproduces the full grid's system when at least two cells of
+    air or solid separate the liquid from the window's sides)."""
     h = 1.0 / n
     dt = 1e-3
     lo, hi = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
     phiL = lambda X: np.maximum(np.hypot(X[0] - 0.5, X[2] - 0.5) - 0.05, X[1] - 0.6)
     phiS = lambda X: np.minimum(box_phi(X, lo, hi), X[1] - 0.1)
     vy = -0.5 - 9.81 * dt
-    return from_functions(f"column{n}", 3, (n, n, n), h, dt, (0.0, 0.0, 0.0), phiL, phiS,
+    dims, origin = (n, n, n), (0.0, 0.0, 0.0)
+    if window is not None:
+        i0, j0, k0, ni, nj, nk = window
+        dims, origin = (ni, nj, nk), (i0 * h, j0 * h, k0 * h)
+    return from_functions(f"column{n}", 3, dims, h, dt, origin, phiL, phiS,
                  lambda P: 1000.0, lambda P: 10.0, lambda d, P: 0.0,
                  lambda d, P: (vy if d == 1 else 0.0))
 
