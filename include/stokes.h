@@ -323,20 +323,25 @@ stokes_status stokes_net_train_step(stokes_net net, int B, int D, int H, int W, 
  * the Jacobi-scaled residual sqrt(m_f) r_f normalised to unit RMS over the
  * active unknowns, and log(m_f)/16 (m = inverse diagonal of A), one channel
  * per unknown field each, zero-padded to cin = 8 (2D) or 12 (3D); its output
- * channels (cout = 4 or 8) give the preconditioned residual
- * z_f = sqrt(m_f) out_f rms on active unknowns.  With options.precond = 1
+ * channels (cout = 4 or 8) correct the Jacobi step:
+ * z_f = m_f r_f + sqrt(m_f) out_f rms on active unknowns (z = r on inactive
+ * ones), so a zero network is plain Jacobi.  With options.precond = 1
  * (mode FP32 or BF16) the inner solve is flexible CG (Polak-Ribiere beta)
  * with this preconditioner, falling back to the Jacobi direction for a step
- * whose network direction fails r.z > 0, inside the same FP64 refinement
- * loop.  Re-attach after every stokes_build_weights.
+ * whose network direction fails r.z > 0, and to plain Jacobi-PCG for the rest
+ * of an inner solve whose residual norm does not halve within 100 iterations,
+ * inside the same FP64 refinement loop.  Re-attach after every
+ * stokes_build_weights.
  */
 stokes_status stokes_set_learned_preconditioner(stokes_ctx ctx, stokes_net net);
 stokes_status stokes_learned_grid(stokes_ctx ctx, int* D, int* H, int* W, int* cin, int* cout);
 /* Network input for an FP64 slot-layout residual r (device) into x (device,
  * FP32, D*H*W*cin); *rms receives the normalisation used. */
 stokes_status stokes_learned_features(stokes_ctx ctx, const double* r, float* x, double* rms);
-/* Training target for an FP64 slot-layout error e with the rms of its
- * residual: y_f = e_f / (sqrt(m_f) rms) on active unknowns, 0 elsewhere. */
+/* Training target for an FP64 slot-layout vector e with the rms of its
+ * residual: y_f = e_f / (sqrt(m_f) rms) on active unknowns, 0 elsewhere.
+ * For the preconditioner above, pass e = err - M_J A err (the part of the
+ * error err that the Jacobi step misses). */
 stokes_status stokes_learned_targets(stokes_ctx ctx, const double* e, double rms, float* y);
 /* Steps at which the flexible CG fell back to the Jacobi direction. */
 long stokes_learned_jacobi_steps(stokes_ctx ctx);
@@ -350,6 +355,21 @@ long stokes_learned_jacobi_steps(stokes_ctx ctx);
  * none). */
 stokes_status stokes_apply_preconditioner(stokes_ctx ctx, int which, const float* r, float* z);
 double stokes_schwarz_setup_ms(stokes_ctx ctx);
+/* Allocation-free form of stokes_apply_preconditioner(ctx, 2, r, z); the
+ * paper has no counterpart (it is an interface for callers that cannot
+ * allocate device memory while they run: a process whose device memory is
+ * reserved up front by its own pool, or a real-time loop that cannot accept
+ * the device-wide synchronisation of cudaMalloc/cudaFree).  Same arguments,
+ * layout and result; it allocates nothing, host or device: its scratch is a
+ * fixed 8 MiB device array inside the library, which bounds the grid to about
+ * 540^2 (larger grids: STOKES_ERR_ARG with the sizes in stokes_last_error).
+ * The context's Schwarz plan must already exist (an earlier
+ * stokes_apply_preconditioner(ctx, 2, ...) or a solve with precond = 2 after
+ * the last weight build), else STOKES_ERR_STATE.  The array's address is
+ * looked up on the first call on each device, with that device current: make
+ * that first call before any stream capture.  Calls share the array: calls
+ * that overlap on the GPU race.  Synchronises the context's stream. */
+stokes_status stokes_apply_schwarz_noalloc(stokes_ctx ctx, const float* r, float* z);
 
 /* Number of tiles holding an active unknown (2D tiles are 32 x 8 slots,
  * 3D tiles 32 x 4 x 4); every CG kernel launches one CTA per such tile. */

@@ -16,6 +16,7 @@ cudaError_t launch_unpack(Ctx* c, const double* slots, double* const* fields, in
 void apply_set_attributes();
 cudaError_t bench_cg_kernels(Ctx* c, int precision, int launches, double* ms_apply, double* ms_update);
 cudaError_t apply_preconditioner(Ctx* c, int which, const float* r, float* z);
+cudaError_t apply_schwarz_noalloc(Ctx* c, const float* r, float* z, std::string* why);
 double schwarz_setup_ms(Ctx* c);
 }  // namespace stk
 
@@ -30,6 +31,23 @@ extern "C" stokes_status stokes_apply_preconditioner(stokes_ctx h, int which, co
 }
 
 extern "C" double stokes_schwarz_setup_ms(stokes_ctx h) { return h ? schwarz_setup_ms(&h->c) : -1.0; }
+
+// Allocation-free variant of stokes_apply_preconditioner(which = 2); the
+// scratch lives in a fixed device array (see apply_schwarz_noalloc).
+extern "C" stokes_status stokes_apply_schwarz_noalloc(stokes_ctx h, const float* r, float* z) {
+    if (!h || !r || !z || r == z) return STOKES_ERR_ARG;
+    Ctx& c = h->c;
+    if (!c.have_weights) { c.err = "stokes_build_weights has not run"; return STOKES_ERR_STATE; }
+    std::string why;
+    cudaError_t e = apply_schwarz_noalloc(&c, r, z, &why);
+    if (e == cudaSuccess) return STOKES_OK;
+    if (e == cudaErrorNotReady) { c.err = why; return STOKES_ERR_STATE; }
+    if (e == cudaErrorInvalidValue) { c.err = why; return STOKES_ERR_ARG; }
+    if (e == cudaErrorLaunchTimeout) { c.err = why; return STOKES_ERR_TIMEOUT; }
+    c.err = std::string("allocation-free Schwarz apply failed: ") + (why.empty() ? "" : why + ": ") +
+            cudaGetErrorString(e);
+    return STOKES_ERR_CUDA;
+}
 
 extern "C" stokes_status stokes_bench_cg_kernels(stokes_ctx h, int precision, int launches, double* ms_apply,
                                                  double* ms_update) {

@@ -18,6 +18,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <string>
 #include <vector>
 #include "internal.cuh"
 #include "ctx.cuh"
@@ -691,6 +693,100 @@ cudaError_t apply_preconditioner(Ctx* c, int which, const float* r, float* z) {
 }
 
 double schwarz_setup_ms(Ctx* c) { return c->sw_ready ? c->sw_setup_ms : -1.0; }
+
+// ---------------------------------------------------------------------------
+// Allocation-free additive Schwarz apply.  For callers that cannot allocate
+// device memory while they run: a process whose device memory is reserved up
+// front by its own pool allocator (cudaMalloc would fail or break its budget),
+// or a real-time loop that cannot accept the implicit device-wide
+// synchronisation of cudaMalloc/cudaFree.  It runs the same kernels as
+// apply_preconditioner(which = 2) with their scratch (the per-patch local
+// results, the block partials, the reduction counter and the CG scalars) in
+// the file-scope device array below instead of context memory, and allocates
+// nothing, host or device.  The patch factors themselves are the context's
+// (built by an earlier Schwarz apply or solve).
+//
+// The array's device address is looked up once per device, with that device
+// current, on the first call on it; make that first call before any stream
+// capture.  Every call uses the same array: calls that overlap on the GPU
+// (other streams, other contexts, other threads) race and give wrong results.
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(8) << 20;   // 8 MiB: 2D grids up to about 540^2
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mu;
+
+static size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// byte offsets of the scratch parts for this context: scalars, counter,
+// partials, local results
+struct NoallocLayout { size_t sc, counter, partial, ybuf, total; };
+static NoallocLayout noalloc_layout(const Ctx* c) {
+    NoallocLayout o;
+    const size_t ng = (size_t)c->sw->npx * c->sw->npy;
+    o.sc = 0;
+    o.counter = round256(2 * sizeof(CgScalars));
+    o.partial = o.counter + 256;
+    o.ybuf = o.partial + round256(sizeof(double) * 2 * ((size_t)c->ntiles_active + 32));
+    o.total = o.ybuf + round256(sizeof(float) * ng * PMAX);
+    return o;
+}
+
+cudaError_t apply_schwarz_noalloc(Ctx* c, const float* r, float* z, std::string* why) {
+    const Layout& L = c->L;
+    if (L.dim != 2) { *why = "the Schwarz preconditioner is 2D only"; return cudaErrorInvalidValue; }
+    if (!c->sw_ready || !c->sw) {
+        *why = "no Schwarz plan for these weights: call stokes_apply_preconditioner(which = 2) or a solve with "
+               "precond = 2 first (that call builds it and may allocate)";
+        return cudaErrorNotReady;
+    }
+    const NoallocLayout lo = noalloc_layout(c);
+    if (lo.total > NOALLOC_SCRATCH_BYTES) {
+        *why = "grid too large for the allocation-free scratch: needs " + std::to_string(lo.total) +
+               " bytes, the fixed maximum is " + std::to_string(NOALLOC_SCRATCH_BYTES) +
+               " (2D grids up to about 540^2); use stokes_apply_preconditioner";
+        return cudaErrorInvalidValue;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) { *why = "device index out of range"; return cudaErrorInvalidDevice; }
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) { *why = "cudaGetSymbolAddress failed"; return e; }
+            g_noalloc_ptr[dev] = p;
+        }
+        base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+    }
+    CgScalars* sc = reinterpret_cast<CgScalars*>(base + lo.sc);
+    unsigned* counter = reinterpret_cast<unsigned*>(base + lo.counter);
+    double* partial = reinterpret_cast<double*>(base + lo.partial);
+    SchwarzPlan P = *c->sw;
+    P.ybuf = reinterpret_cast<float*>(base + lo.ybuf);
+    cudaStream_t s = c->stream;
+    const int64_t V = c->vec_elems();
+    // what must start at zero: the scalars (done, status), the counter and
+    // the local results (inactive patches and positions are summed as zeros)
+    if ((e = cudaMemsetAsync(base, 0, lo.total, s)) != cudaSuccess) return e;
+    // inactive tiles: identity on real slots (r is zero on padding)
+    if ((e = cudaMemcpyAsync(z, r, sizeof(float) * V, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+    CgWork<float> w{};
+    w.r = (float*)r;
+    w.z = z;
+    const int nb = c->ntiles_active;
+    launch_schwarz_gemv(L, P, r, sc, s);
+    if (nb) k_sw_finish<1><<<nb, 256, 0, s>>>(L, c->tiles, c->A, P, w, sc, partial, counter, nb, 0, 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int status = 0;
+    if ((e = cudaMemcpyAsync(&status, &sc->status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if (status == STOKES_ERR_TIMEOUT) { *why = "a local solve's copy wait timed out"; return cudaErrorLaunchTimeout; }
+    return cudaSuccess;
+}
 
 // Time real CG iterations kernel by kernel: r = b (the last right-hand side),
 // then ``launches`` x [apply in CG mode, update] with CUDA events around each

@@ -52,7 +52,8 @@ EXPORTED = ("stokes_create", "stokes_destroy", "stokes_last_error", "stokes_buil
             "stokes_net_layer", "stokes_net_set_params", "stokes_net_get_params", "stokes_net_forward",
             "stokes_net_gradient", "stokes_net_train_step", "stokes_set_learned_preconditioner",
             "stokes_learned_grid", "stokes_learned_features", "stokes_learned_targets",
-            "stokes_learned_jacobi_steps", "stokes_apply_preconditioner", "stokes_schwarz_setup_ms")
+            "stokes_learned_jacobi_steps", "stokes_apply_preconditioner", "stokes_schwarz_setup_ms",
+            "stokes_apply_schwarz_noalloc")
 
 
 class BatchIO(C.Structure):
@@ -112,6 +113,7 @@ def load_library(path=LIB_PATH):
         "stokes_learned_jacobi_steps": (C.c_long, [P]),
         "stokes_apply_preconditioner": (I, [P, I, P, P]),
         "stokes_schwarz_setup_ms": (D, [P]),
+        "stokes_apply_schwarz_noalloc": (I, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -266,6 +268,12 @@ class StokesContext:
     def apply_preconditioner(self, which, r32, z32):
         self._check(self.lib.stokes_apply_preconditioner(self.h, which, _dev(r32, torch.float32).data_ptr(),
                                                          _dev(z32, torch.float32).data_ptr()))
+
+    def apply_schwarz_noalloc(self, r32, z32):
+        """Allocation-free Schwarz apply (same result as apply_preconditioner(2));
+        the plan must exist.  For callers that cannot allocate device memory."""
+        self._check(self.lib.stokes_apply_schwarz_noalloc(self.h, _dev(r32, torch.float32).data_ptr(),
+                                                          _dev(z32, torch.float32).data_ptr()))
 
     def schwarz_setup_ms(self):
         return self.lib.stokes_schwarz_setup_ms(self.h)
@@ -441,6 +449,11 @@ def learned_grid(ctx):
 def attach_network(ctx, net):
     ctx._check(ctx.lib.stokes_set_learned_preconditioner(ctx.h, net.h if net is not None else None))
     ctx._net = net
+
+
+def learned_jacobi_steps(ctx):
+    """Jacobi fallback steps taken by the last learned-preconditioner solve."""
+    return int(ctx.lib.stokes_learned_jacobi_steps(ctx.h))
 
 
 def learned_features(ctx, r):
