@@ -6,13 +6,18 @@
 //   [ log(m_f) / 16      for each unknown field f ]  (operator information)
 //   zero channels up to the network's cin;
 // m_f is the Jacobi inverse diagonal (1 on inactive unknowns, 0 on padding).
-// Output channel f gives z_f = sqrt(m_f) out_f / s on active unknowns; an
-// inactive unknown keeps z = r (its row is the identity).
+// The network corrects the Jacobi step: output channel f gives
+// z_f = m_f r_f + sqrt(m_f) out_f / s on active unknowns (a zero network is
+// plain Jacobi); an inactive unknown keeps z = r (its row is the identity).
+// Training targets are therefore the part of the error that the Jacobi step
+// misses, e - M_J A e, in the same scaling.
 //
 // Flexible CG (Polak-Ribiere): beta = r_{k+1}.(z_{k+1} - z_k) / r_k.z_k, so a
 // preconditioner that is not a fixed linear operator still gives a
 // convergent method; if the network direction fails r.z > 0 the iteration
-// falls back to the Jacobi direction for that step.  Vectors are FP32; the
+// falls back to the Jacobi direction for that step, and if the residual norm
+// does not halve within 100 iterations the rest of the inner solve is plain
+// Jacobi-PCG.  Vectors are FP32; the
 // refinement loop around it (pcg.cu) recomputes the true residual in FP64.
 #include <cmath>
 #include <cstdio>
@@ -93,7 +98,7 @@ __global__ void k_unfeatures(Layout L, int nf, const float* out, const float* r,
         int64_t of = (int64_t)f * L.stride + o;
         float m = minv[of];
         float zz;
-        if (act_site[site][o]) zz = sqrtf(m) * out[v * g.cout + f] * inv_s;
+        if (act_site[site][o]) zz = m * r[of] + sqrtf(m) * out[v * g.cout + f] * inv_s;
         else zz = m > 0.f ? r[of] : 0.f;
         z[of] = zz;
     }
@@ -260,6 +265,13 @@ cudaError_t run_inner_fpcg(Ctx* c, stokes_net_s* net, double scale, double tol_r
     int it = 0;
     const double tol2 = tol_rel * tol_rel * rr0;
     double rr = rr0;
+    // progress check: every FPCG_WINDOW iterations the residual norm must at
+    // least halve, else the rest of this solve uses the Jacobi direction
+    // (plain PCG), so a poor network costs at most one window
+    constexpr int FPCG_WINDOW = 100;
+    bool jacobi_only = false;
+    int win_it = 0;
+    double win_rr = rr0;
     while (it < max_iter && rr > tol2 && rr0 > 0) {
         // p = z + beta p_old, q = A p, alpha = rz / p.q
         cudaMemcpyAsync(c->sc, &hs, sizeof(CgScalars), cudaMemcpyHostToDevice, s);
@@ -274,7 +286,12 @@ cudaError_t run_inner_fpcg(Ctx* c, stokes_net_s* net, double scale, double tol_r
             return e;
         k_xr_update<<<nb, 256, 0, s>>>(L, c->tiles, c->nf, w.x, w.r, w.p[(it & 1) ^ 1], w.q, c->sc);
         cudaMemcpyAsync(zold, w.z, sizeof(float) * V, cudaMemcpyDeviceToDevice, s);
-        if ((e = precondition(c, net, w.r, w.z)) != cudaSuccess) return e;
+        if (jacobi_only) {
+            k_jacobi_dir<<<nb256(V), 256, 0, s>>>(V, w.r, c->A.minv32, w.z);
+            ++jac;
+        } else if ((e = precondition(c, net, w.r, w.z)) != cudaSuccess) {
+            return e;
+        }
         k_dots3<<<nb, 256, 0, s>>>(L, c->tiles, c->nf, w.r, w.z, zold, c->partial, c->counter, nb, d3);
         cudaMemcpyAsync(h3, d3, sizeof(h3), cudaMemcpyDeviceToHost, s);
         CgScalars back{};
@@ -299,6 +316,15 @@ cudaError_t run_inner_fpcg(Ctx* c, stokes_net_s* net, double scale, double tol_r
         hs.beta = std::fmax(0.0, (rz_new - rz_old) / hs.rz);
         hs.rz = rz_new;
         hs.done = 0;
+        if (!jacobi_only && it - win_it >= FPCG_WINDOW) {
+            if (rr > 0.25 * win_rr) {
+                jacobi_only = true;
+                if (verbose) std::fprintf(stderr, "[stokes] fpcg it %d: residual fell %.2fx in %d steps, Jacobi from here\n",
+                                          it, std::sqrt(win_rr / rr), FPCG_WINDOW);
+            }
+            win_it = it;
+            win_rr = rr;
+        }
     }
     // hand the result to the refinement loop like the Jacobi path does
     CgScalars res{};

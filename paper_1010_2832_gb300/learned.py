@@ -1,12 +1,14 @@
 """Training data, training loop and evaluation of the learned preconditioner.
 
-Pairs come from the solver itself, as in the classic error-correction
-setting: for a smooth random error field e on the active unknowns, the
-residual it leaves is r = A e (one FP64 apply on the GPU).  The network is
-trained to map the normalised, Jacobi-scaled residual to the matching
-error (see stokes_learned_features / stokes_learned_targets).  Everything
-runs on the GPU through the C ABI; the random fields are seeded inputs
-built on the host.
+Pairs come from the solver itself.  A seeded start error e0 on the active
+unknowns (white noise or a sum of smooth Fourier modes) defines b = A e0;
+k iterations of Jacobi-preconditioned CG on A x = b from x = 0 leave the
+error e = e0 - x_k, rich in exactly the components Jacobi-PCG is slow to
+remove (k = 0 keeps e0).  The residual is r = A e.  The preconditioner
+adds a network correction to the Jacobi step, so the training target is
+the part of e that the Jacobi step misses, e - M_J r, scaled as
+stokes_learned_targets describes.  Everything runs on the GPU through the
+C ABI; the random fields are seeded inputs built on the host.
 """
 import time
 
@@ -37,17 +39,38 @@ def smooth_error(ctx, wl, seed, modes=6):
     return ctx.fields_to_slots(torch.from_numpy(e).cuda())
 
 
-def make_pairs(ctx, wl, n_pairs, seed0):
-    """(features, targets) device tensors for n_pairs smooth errors."""
+def white_error(ctx, seed):
+    """Seeded white-noise error in FP64 slot layout, zero on inactive unknowns."""
+    rng = np.random.default_rng(seed)
+    act = ctx.export(3).cpu().numpy().astype(bool)
+    e = rng.normal(size=act.size) * act
+    return ctx.fields_to_slots(torch.from_numpy(e).cuda())
+
+
+def make_pairs(ctx, wl, n_pairs, seed0, cg_iters=(0, 4, 16, 64, 256)):
+    """(features, targets) device tensors for n_pairs solver-generated errors.
+
+    Pair q starts from white noise (even q) or smooth modes (odd q) and runs
+    cg_iters[q % len(cg_iters)] Jacobi-PCG iterations on it."""
     xs, ys = [], []
-    Ae = ctx.new_vector()
+    b = ctx.new_vector()
+    x = ctx.new_vector()
+    r = ctx.new_vector()
+    z32 = ctx.new_vector(torch.float32)
     for q in range(n_pairs):
-        e = smooth_error(ctx, wl, seed0 + q)
-        ctx.apply(e, Ae, stokes.FP64)
-        x, rms = stokes.learned_features(ctx, Ae)
-        y = stokes.learned_targets(ctx, e, rms)
-        xs.append(x)
-        ys.append(y)
+        e0 = white_error(ctx, seed0 + q) if q % 2 == 0 else smooth_error(ctx, wl, seed0 + q)
+        k = cg_iters[q % len(cg_iters)]
+        e = e0
+        if k > 0:
+            ctx.apply(e0, b, stokes.FP64)
+            x.zero_()
+            ctx.solve_system(b, x, stokes.default_options(mode=stokes.FP64, precond=0, tol=1e-300, max_iter=k))
+            e = e0 - x
+        ctx.apply(e, r, stokes.FP64)
+        feats, rms = stokes.learned_features(ctx, r)
+        ctx.apply_preconditioner(0, r.float(), z32)
+        ys.append(stokes.learned_targets(ctx, e - z32.double(), rms))
+        xs.append(feats)
     return xs, ys
 
 
