@@ -32,17 +32,28 @@ sys.path.insert(0, ROOT)
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM traffic per launch of the CG-mode apply measured with ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the source
-# hash it was taken with; see profiles/.
+# Source files of each reported kernel (the ncu traffic below is valid only
+# for the hash of these files it was taken with; see profiles/).
+KERNEL_SOURCES = {
+    "k_schwarz_gemv": ("schwarz.cuh", "internal.cuh", "ctx.cuh"),
+    "k_apply2d": ("apply.cu", "apply2d_tile.cuh", "internal.cuh", "ctx.cuh"),
+    "k_apply3d": ("apply.cu", "internal.cuh", "ctx.cuh"),
+}
+# (workload, mode, kernel) -> (source hash, dram__bytes_read.sum +
+# dram__bytes_write.sum per launch from one ncu capture of the same command)
 NCU_TRAFFIC = {}
 
 
-def kernel_source_hash():
+def kernel_source_hash(kernel):
     h = hashlib.sha256()
-    for f in ("apply.cu", "internal.cuh", "ctx.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_1010_2832_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, mode, kernel):
+    tr = NCU_TRAFFIC.get((workload, mode, kernel))
+    return tr[1] if tr and tr[0] == kernel_source_hash(kernel) else None
 
 
 def hbm_peak():
@@ -285,17 +296,36 @@ def run_ours(args, rank, world):
             e2e_times.append(ev0.elapsed_time(ev1))
     e2e_ms = float(np.mean(e2e_times))
 
-    # ---- roofline of the dominant kernel (CG-mode apply) -----------------
+    # ---- roofline of the dominant kernel ----------------------------------
     prec = mode_id(args.mode)
+    peak, peak_kind = hbm_peak()
     ms_apply, ms_update = ctx.bench_cg_kernels(prec, 50)
     tiles = ctx.active_tiles()
     slots = tiles * (256 if wl.dim == 2 else 512)
-    alg_bytes = slots * bytes_per_slot_apply(wl.dim, prec)
-    achieved = alg_bytes / (ms_apply * 1e-3) / 1e9
-    peak, peak_kind = hbm_peak()
-    src_hash = kernel_source_hash()
-    tr = NCU_TRAFFIC.get((args.workload, args.mode))
-    traffic = tr[1] if tr and tr[0] == src_hash else None
+    apply_kernel = "k_apply2d" if wl.dim == 2 else "k_apply3d"
+    apply_bytes = slots * bytes_per_slot_apply(wl.dim, prec)
+    apply_gbs = apply_bytes / (ms_apply * 1e-3) / 1e9
+    if precond == 2:
+        ms_local, ms_gather, local_bytes = ctx.bench_schwarz_kernels(50)
+        achieved = local_bytes / (ms_local * 1e-3) / 1e9
+        roofline = {"kernel": "k_schwarz_gemv (local patch solves of the Schwarz preconditioner)", "bound": "hbm",
+                    "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_source": peak_kind, "traffic": ncu_traffic(args.workload, args.mode, "k_schwarz_gemv"),
+                    "ms_per_launch": ms_local, "bytes_per_launch": local_bytes,
+                    "units_per_launch": "every active patch (4x4-slot core + ring)",
+                    "gather_ms_per_launch": ms_gather, "source_hash": kernel_source_hash("k_schwarz_gemv")}
+    else:
+        roofline = {"kernel": f"{apply_kernel} (CG mode: p = z + beta p, q = A p, p.q)", "bound": "hbm",
+                    "achieved": apply_gbs, "peak": peak, "unit": "GB/s", "frac": apply_gbs / peak,
+                    "peak_source": peak_kind, "traffic": ncu_traffic(args.workload, args.mode, apply_kernel),
+                    "ms_per_launch": ms_apply, "bytes_per_launch": apply_bytes, "units_per_launch": slots,
+                    "bytes_per_unit": bytes_per_slot_apply(wl.dim, prec), "update_ms_per_launch": ms_update,
+                    "source_hash": kernel_source_hash(apply_kernel)}
+    stencil = {"kernel": f"{apply_kernel} (CG mode)", "workload": args.workload, "achieved": apply_gbs,
+               "unit": "GB/s", "frac": apply_gbs / peak, "ms_per_launch": ms_apply, "bytes_per_launch": apply_bytes,
+               "update_ms_per_launch": ms_update}
+    if not args.no_dense_apply:
+        stencil["dense"] = dense_apply(wl.dim, prec, peak)
     out = {
         "metric": "time-to-solution per implicit step at 1e-8 rel. residual",
         "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -312,15 +342,39 @@ def run_ours(args, rank, world):
                    "steps_per_s_all_ranks": world * 1000.0 / ms},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
         "gpu_launches": launches * args.steps,
-        "roofline": {"kernel": "k_apply (CG mode: p = z + beta p, q = A p, p.q)", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_source": peak_kind, "traffic": traffic, "ms_per_launch": ms_apply,
-                     "bytes_per_launch": alg_bytes, "units_per_launch": slots,
-                     "bytes_per_unit": bytes_per_slot_apply(wl.dim, prec), "update_ms_per_launch": ms_update,
-                     "source_hash": src_hash},
+        "roofline": roofline,
+        "stencil_apply": stencil,
         "clocks": clk.summary(),
     }
     return out, wl
+
+
+def dense_apply(dim, prec, peak):
+    """The CG-mode apply on a box full of liquid (2D 4096^2 or 3D 256^3), where
+    every tile is active: the stencil's streaming bandwidth at scale."""
+    import torch
+    from paper_1010_2832_gb300 import stokes, workloads as W
+    n = 4096 if dim == 2 else 256
+    wl = W.full_box(n, dim)
+    ctx, d = stokes.context_for(wl)
+    if dim == 2:
+        sizes = [n * n, (n + 1) ** 2, n * n]
+    else:
+        sizes = [n ** 3, n ** 3, n * (n + 1) ** 2, n * (n + 1) ** 2, n * (n + 1) ** 2, n ** 3]
+    u = [torch.zeros_like(t) for t in d["u_star"]]
+    taus = [torch.zeros(s, dtype=torch.float64, device=u[0].device) for s in sizes[:-1]]
+    p = torch.zeros(sizes[-1], dtype=torch.float64, device=u[0].device)
+    ctx.solve_step(d["u_star"], u, taus, p, stokes.default_options(mode=prec, precond=0, max_iter=4))
+    ms_a, ms_u = ctx.bench_cg_kernels(prec, 30)
+    slots = ctx.active_tiles() * (256 if dim == 2 else 512)
+    by = slots * bytes_per_slot_apply(dim, prec)
+    gbs = by / (ms_a * 1e-3) / 1e9
+    ctx.close()
+    del u, taus, p, d
+    torch.cuda.empty_cache()
+    return {"workload": f"{dim}D {n}^{dim} box full of liquid", "achieved": gbs, "frac": gbs / peak,
+            "ms_per_launch": ms_a, "bytes_per_launch": by, "units_per_launch": slots,
+            "bytes_per_unit": bytes_per_slot_apply(dim, prec)}
 
 
 def cpu_sample(wl, n_iter_fp64, budget_s=12.0):
@@ -401,12 +455,14 @@ def main():
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dense-apply", action="store_true", help="skip the dense-box apply measurement")
     ap.add_argument("--quick", action="store_true", help="timed steps only (for profiler runs)")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven CG loop (profilers cannot enter conditional graphs)")
     args = ap.parse_args()
     if args.quick:
         args.no_cpu_baseline = True
+        args.no_dense_apply = True
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -240,6 +240,16 @@ double stokes_last_apply_ms(stokes_ctx ctx);
  * (ms) of the CG-mode apply kernel (direction update, A p and p.Ap fused)
  * and of the vector-update kernel.  Overwrites the solver's work vectors.
  * Synchronises. */
+/* Measurement support for the Schwarz path (2D): ``launches`` times the two
+ * preconditioner kernels of an FP32 Schwarz-CG iteration (right-hand side =
+ * the last one stokes_solve_step built), CUDA events around each on the
+ * context's stream; mean device ms of the local patch solves and of the
+ * gather (z, r.z, r.r); *bytes_local = algorithmic bytes of one local-solve
+ * launch (every active patch's stored factor X = L^-1, its residual gather,
+ * scaling, local map and results).  Builds the patch factors if needed.
+ * Overwrites the solver's work vectors.  Synchronises. */
+stokes_status stokes_bench_schwarz_kernels(stokes_ctx ctx, int launches, double* ms_local, double* ms_gather,
+                                           double* bytes_local);
 stokes_status stokes_bench_cg_kernels(stokes_ctx ctx, int precision, int launches, double* ms_apply,
                                       double* ms_update);
 

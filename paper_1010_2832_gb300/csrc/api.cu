@@ -15,6 +15,7 @@ void set_error(Ctx* c, const std::string& m) { c->err = m; }
 cudaError_t launch_unpack(Ctx* c, const double* slots, double* const* fields, int to_fields);
 void apply_set_attributes();
 cudaError_t bench_cg_kernels(Ctx* c, int precision, int launches, double* ms_apply, double* ms_update);
+cudaError_t bench_schwarz_kernels(Ctx* c, int launches, double* ms_local, double* ms_gather, double* bytes_local);
 cudaError_t apply_preconditioner(Ctx* c, int which, const float* r, float* z);
 cudaError_t apply_schwarz_noalloc(Ctx* c, const float* r, float* z, std::string* why);
 double schwarz_setup_ms(Ctx* c);
@@ -47,6 +48,18 @@ extern "C" stokes_status stokes_apply_schwarz_noalloc(stokes_ctx h, const float*
     c.err = std::string("allocation-free Schwarz apply failed: ") + (why.empty() ? "" : why + ": ") +
             cudaGetErrorString(e);
     return STOKES_ERR_CUDA;
+}
+
+extern "C" stokes_status stokes_bench_schwarz_kernels(stokes_ctx h, int launches, double* ms_local,
+                                                      double* ms_gather, double* bytes_local) {
+    if (!h || !ms_local || !ms_gather || !bytes_local || launches < 1) return STOKES_ERR_ARG;
+    Ctx& c = h->c;
+    if (!c.have_weights) { c.err = "stokes_build_weights has not run"; return STOKES_ERR_STATE; }
+    if (c.L.dim != 2) { c.err = "the Schwarz preconditioner is 2D only"; return STOKES_ERR_ARG; }
+    if (c.ntiles_active == 0) { c.err = "no active unknowns"; return STOKES_ERR_STATE; }
+    cudaError_t e = bench_schwarz_kernels(&c, launches, ms_local, ms_gather, bytes_local);
+    if (e != cudaSuccess) { c.err = std::string("Schwarz kernel timing failed: ") + cudaGetErrorString(e); return STOKES_ERR_CUDA; }
+    return STOKES_OK;
 }
 
 extern "C" stokes_status stokes_bench_cg_kernels(stokes_ctx h, int precision, int launches, double* ms_apply,

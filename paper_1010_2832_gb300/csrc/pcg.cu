@@ -136,13 +136,12 @@ __global__ void __launch_bounds__(256) k_cg_init(Layout L, const int* __restrict
 template <class T>
 __global__ void __launch_bounds__(256) k_cg_update(Layout L, const int* __restrict__ tiles, int nf,
                                                    const T* __restrict__ minv, CgWork<T> w, const T* __restrict__ p,
-                                                   CgScalars* sc, double* partial, unsigned* counter, int nblocks,
+                                                   CgScalars* sc, double* partial, unsigned* counter, int ntiles,
                                                    cudaGraphConditionalHandle h, int use_cond) {
     if (sc->done) {
         if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
         return;
     }
-    const int tile = tiles[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T alpha = (T)sc->alpha;
     AccT<T> rz, rr;
@@ -151,6 +150,9 @@ __global__ void __launch_bounds__(256) k_cg_update(Layout L, const int* __restri
     T* __restrict__ Rr = w.r;
     T* __restrict__ Z = w.z;
     const T* __restrict__ Q = w.q;
+    // persistent over the tile list: one block reduction per CTA
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+    const int tile = tiles[k];
     for (int row = warp; row < nrow; row += 8) {
         const int64_t o = tile_row_off(L, tile, row) + lane;
         // issue every load of the slot's fields before any store
@@ -174,8 +176,9 @@ __global__ void __launch_bounds__(256) k_cg_update(Layout L, const int* __restri
             }
         }
     }
+    }
     double a = rz.warp(), b = rr.warp();
-    block_partial2(a, b, partial, counter, nblocks, [&](double trz, double trr) {
+    block_partial2(a, b, partial, counter, gridDim.x, [&](double trz, double trr) {
         sc->rr = trr;
         sc->iter += 1;
         if (!isfinite(trr) || !isfinite(trz)) { sc->done = 1; sc->status = STOKES_ERR_NONFINITE; }
@@ -217,17 +220,20 @@ __global__ void __launch_bounds__(256) k_sw_init(Layout L, const int* __restrict
 template <int INIT>
 __global__ void __launch_bounds__(256) k_sw_finish(Layout L, const int* __restrict__ tiles, DevArrays D,
                                                    SchwarzPlan P, CgWork<float> w, CgScalars* sc, double* partial,
-                                                   unsigned* counter, int nblocks, cudaGraphConditionalHandle h,
+                                                   unsigned* counter, int ntiles, cudaGraphConditionalHandle h,
                                                    int use_cond) {
     if (!INIT && sc->done) {
         if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
         return;
     }
-    const int tile = tiles[blockIdx.x];
-    const int c0 = (tile % L.ntx) * TX, r0 = (tile / L.ntx) * TY2;
     double rz = 0.0, rr = 0.0;
-    schwarz_gather_slot(L, D, P, w.r, w.z, c0 + (threadIdx.x & 31), r0 + (threadIdx.x >> 5), rz, rr);
-    block_partial2(warp_sum(rz), warp_sum(rr), partial, counter, nblocks, [&](double trz, double trr) {
+    // persistent over the tile list: one block reduction per CTA
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const int tile = tiles[k];
+        const int c0 = (tile % L.ntx) * TX, r0 = (tile / L.ntx) * TY2;
+        schwarz_gather_slot(L, D, P, w.r, w.z, c0 + (threadIdx.x & 31), r0 + (threadIdx.x >> 5), rz, rr);
+    }
+    block_partial2(warp_sum(rz), warp_sum(rr), partial, counter, gridDim.x, [&](double trz, double trr) {
         if (INIT) {
             const bool timed_out = sc->status == STOKES_ERR_TIMEOUT;   // set by a local solve
             sc->rz = trz; sc->rr = trr; sc->rr0 = trr;
@@ -310,6 +316,28 @@ static cudaError_t schwarz_build(Ctx* c) {
     return cudaGetLastError();
 }
 
+// CTAs of a persistent tile kernel: min(tiles, the CTAs resident on the
+// device at once), cached per kernel.
+static int persist_grid(const void* fn, int ntiles, size_t smem = 0) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void*, int>> cache;
+    int res = 0;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        for (auto& kv : cache)
+            if (kv.first == fn) res = kv.second;
+        if (!res) {
+            int dev = 0, sms = 0, per = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 256, smem);
+            res = std::max(1, sms) * std::max(1, per);
+            cache.push_back({fn, res});
+        }
+    }
+    return std::max(1, std::min(ntiles, res));
+}
+
 static void schwarz_body(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond, int parity) {
     const Layout& L = c->L;
     const int nb = c->ntiles_active;
@@ -321,9 +349,10 @@ static void schwarz_body(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, i
     a.counter = c->counter;
     a.sc = c->sc;
     launch_apply_mode<float, float>(L, c->tiles, nb, c->coef<float>(), w.z, w.q, MODE_CG, a, s);
-    k_cg_xr<<<nb, 256, 0, s>>>(L, c->tiles, c->nf, w, w.p[parity ^ 1], c->sc);
+    k_cg_xr<<<persist_grid((const void*)k_cg_xr, nb), 256, 0, s>>>(L, c->tiles, nb, c->nf, w, w.p[parity ^ 1], c->sc);
     launch_schwarz_gemv(L, *c->sw, w.r, c->sc, s);
-    k_sw_finish<0><<<nb, 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc, c->partial, c->counter, nb, h, use_cond);
+    k_sw_finish<0><<<persist_grid((const void*)k_sw_finish<0>, nb), 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc,
+                                                                               c->partial, c->counter, nb, h, use_cond);
 }
 
 static void schwarz_start(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
@@ -332,7 +361,8 @@ static void schwarz_start(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, 
     CgWork<float>& w = c->w32;
     k_sw_init<<<nb, 256, 0, s>>>(L, c->tiles, c->w64.r, w, c->sc);
     launch_schwarz_gemv(L, *c->sw, w.r, c->sc, s);
-    k_sw_finish<1><<<nb, 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc, c->partial, c->counter, nb, h, use_cond);
+    k_sw_finish<1><<<persist_grid((const void*)k_sw_finish<1>, nb), 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc,
+                                                                               c->partial, c->counter, nb, h, use_cond);
 }
 
 // x64 += sign * d / scale (refinement update; sign = -1 undoes it), over active tiles
@@ -420,7 +450,8 @@ static cudaError_t build_inner_graph(Ctx* c, CgWork<T>& w, const T* minv, const 
         a.counter = cnt;
         a.sc = sc;
         launch_apply_mode<T, C>(L, c->tiles, nb, cf, w.z, w.q, MODE_CG, a, s);
-        k_cg_update<T><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, minv, w, w.p[k ^ 1], sc, part, cnt, nb, h, 1);
+        k_cg_update<T><<<persist_grid((const void*)k_cg_update<T>, nb), 256, 0, s>>>(L, c->tiles, c->nf, minv, w,
+                                                                                   w.p[k ^ 1], sc, part, cnt, nb, h, 1);
     }
     cudaGraph_t cap2 = nullptr;
     if ((e = cudaStreamEndCapture(s, &cap2)) != cudaSuccess) return e;
@@ -464,7 +495,8 @@ static cudaError_t run_inner(Ctx* c, int prec_slot, CgWork<T>& w, const T* minv,
             a.counter = c->counter;
             a.sc = c->sc;
             if ((e = launch_apply_mode<T, C>(L, c->tiles, nb, cf, w.z, w.q, MODE_CG, a, s)) != cudaSuccess) return e;
-            k_cg_update<T><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, minv, w, w.p[(k & 1) ^ 1], c->sc, c->partial,
+            k_cg_update<T><<<persist_grid((const void*)k_cg_update<T>, nb), 256, 0, s>>>(L, c->tiles, c->nf, minv, w,
+                                                                                       w.p[(k & 1) ^ 1], c->sc, c->partial,
                                               c->counter, nb, h0, 0);
         }
         if ((e = fetch_scalars(c)) != cudaSuccess) return e;
@@ -686,7 +718,9 @@ cudaError_t apply_preconditioner(Ctx* c, int which, const float* r, float* z) {
     w.z = z;
     const int nb = c->ntiles_active;
     launch_schwarz_gemv(L, *c->sw, r, c->sc, s);
-    if (nb) k_sw_finish<1><<<nb, 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc, c->partial, c->counter, nb, 0, 0);
+    if (nb)
+        k_sw_finish<1><<<persist_grid((const void*)k_sw_finish<1>, nb), 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc,
+                                                                                   c->partial, c->counter, nb, 0, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = fetch_scalars(c)) != cudaSuccess) return e;
     return c->h_sc[0].status == STOKES_ERR_TIMEOUT ? cudaErrorLaunchTimeout : cudaSuccess;
@@ -779,7 +813,9 @@ cudaError_t apply_schwarz_noalloc(Ctx* c, const float* r, float* z, std::string*
     w.z = z;
     const int nb = c->ntiles_active;
     launch_schwarz_gemv(L, P, r, sc, s);
-    if (nb) k_sw_finish<1><<<nb, 256, 0, s>>>(L, c->tiles, c->A, P, w, sc, partial, counter, nb, 0, 0);
+    if (nb)
+        k_sw_finish<1><<<persist_grid((const void*)k_sw_finish<1>, nb), 256, 0, s>>>(L, c->tiles, c->A, P, w, sc, partial,
+                                                                                   counter, nb, 0, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     int status = 0;
     if ((e = cudaMemcpyAsync(&status, &sc->status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
@@ -813,7 +849,8 @@ static cudaError_t bench_impl(Ctx* c, CgWork<T>& w, const T* minv, const Coef<C>
         a.sc = c->sc;
         launch_apply_mode<T, C>(L, c->tiles, nb, cf, w.z, w.q, MODE_CG, a, s);
         cudaEventRecord(ev[2 * k + 1], s);
-        k_cg_update<T><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, minv, w, w.p[(k & 1) ^ 1], c->sc, c->partial,
+        k_cg_update<T><<<persist_grid((const void*)k_cg_update<T>, nb), 256, 0, s>>>(L, c->tiles, c->nf, minv, w,
+                                                                                   w.p[(k & 1) ^ 1], c->sc, c->partial,
                                           c->counter, nb, h0, 0);
         cudaEventRecord(ev[2 * k + 2], s);
     }
@@ -830,6 +867,59 @@ static cudaError_t bench_impl(Ctx* c, CgWork<T>& w, const T* minv, const Coef<C>
     *ms_update = tu / launches;
     if ((e = fetch_scalars(c)) != cudaSuccess) return e;
     if (c->h_sc[0].done) return cudaErrorInvalidValue;  // the loop stopped early: timings invalid
+    return cudaGetLastError();
+}
+
+// Time the Schwarz kernels of a CG iteration launch by launch (local patch
+// solves, then the gather with its dots), CUDA events around each on the
+// context's stream, r = the last right-hand side.  bytes_local: algorithmic
+// bytes of one local-solve launch (every patch's factor, its residual gather
+// by position, scaling and local map, its results).
+cudaError_t bench_schwarz_kernels(Ctx* c, int launches, double* ms_local, double* ms_gather, double* bytes_local) {
+    const Layout& L = c->L;
+    cudaStream_t s = c->stream;
+    cudaError_t e;
+    if (L.dim != 2) return cudaErrorInvalidValue;
+    if (!c->sw_ready && (e = schwarz_build(c)) != cudaSuccess) return e;
+    const SchwarzPlan& P = *c->sw;
+    std::vector<int> nloc(std::max(1, P.np));
+    if (P.np && (e = cudaMemcpy(nloc.data(), P.nloc, sizeof(int) * P.np, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return e;
+    double by = 0.0;
+    for (int q = 0; q < P.np; ++q)
+        by += (double)tri4_off(nloc[q]) * sizeof(float) + PMAX * (sizeof(float) + sizeof(float) + sizeof(short)) +
+              2 * PR * PR * sizeof(float) + 2 * sizeof(int);
+    *bytes_local = by;
+    if ((e = push_inner_params(c, 1.0, 0.0, 1 << 30)) != cudaSuccess) return e;
+    CgWork<float>& w = c->w32;
+    const int nb = c->ntiles_active;
+    k_sw_init<<<nb, 256, 0, s>>>(L, c->tiles, c->b64, w, c->sc);
+    launch_schwarz_gemv(L, P, w.r, c->sc, s);
+    k_sw_finish<1><<<persist_grid((const void*)k_sw_finish<1>, nb), 256, 0, s>>>(L, c->tiles, c->A, P, w, c->sc,
+                                                                               c->partial, c->counter, nb, 0, 0);
+    std::vector<cudaEvent_t> ev(2 * launches + 1);
+    for (auto& x : ev) cudaEventCreate(&x);
+    cudaEventRecord(ev[0], s);
+    for (int k = 0; k < launches; ++k) {
+        launch_schwarz_gemv(L, P, w.r, c->sc, s);
+        cudaEventRecord(ev[2 * k + 1], s);
+        k_sw_finish<0><<<persist_grid((const void*)k_sw_finish<0>, nb), 256, 0, s>>>(L, c->tiles, c->A, P, w, c->sc,
+                                                                                   c->partial, c->counter, nb, 0, 0);
+        cudaEventRecord(ev[2 * k + 2], s);
+    }
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    double ta = 0, tg = 0;
+    for (int k = 0; k < launches; ++k) {
+        float a = 0, g = 0;
+        cudaEventElapsedTime(&a, ev[2 * k], ev[2 * k + 1]);
+        cudaEventElapsedTime(&g, ev[2 * k + 1], ev[2 * k + 2]);
+        ta += a; tg += g;
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    *ms_local = ta / launches;
+    *ms_gather = tg / launches;
+    if ((e = fetch_scalars(c)) != cudaSuccess) return e;
+    if (c->h_sc[0].done) return cudaErrorInvalidValue;  // the kernels returned early: timings invalid
     return cudaGetLastError();
 }
 

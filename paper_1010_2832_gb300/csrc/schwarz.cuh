@@ -475,28 +475,31 @@ __device__ __forceinline__ void schwarz_gather_slot(const Layout& L, const DevAr
     }
 }
 
-// x += alpha p, r -= alpha q (FP32), no preconditioning
-__global__ void __launch_bounds__(256) k_cg_xr(Layout L, const int* __restrict__ tiles, int nf, CgWork<float> w,
-                                               const float* __restrict__ p, const CgScalars* sc) {
+// x += alpha p, r -= alpha q (FP32), no preconditioning; persistent over the
+// tile list
+__global__ void __launch_bounds__(256) k_cg_xr(Layout L, const int* __restrict__ tiles, int ntiles, int nf,
+                                               CgWork<float> w, const float* __restrict__ p, const CgScalars* sc) {
     if (sc->done) return;
-    const int tile = tiles[blockIdx.x];
-    const int c0 = (tile % L.ntx) * TX, r0 = (tile / L.ntx) * TY2;
-    const int64_t o = L.off(c0 + (threadIdx.x & 31), r0 + (threadIdx.x >> 5), 0);
     const float alpha = (float)sc->alpha;
     float* __restrict__ X = w.x;
     float* __restrict__ R = w.r;
     const float* __restrict__ Q = w.q;
-    float pv[3], xv[3], rv[3], qv[3];
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const int tile = tiles[k];
+        const int c0 = (tile % L.ntx) * TX, r0 = (tile / L.ntx) * TY2;
+        const int64_t o = L.off(c0 + (threadIdx.x & 31), r0 + (threadIdx.x >> 5), 0);
+        float pv[3], xv[3], rv[3], qv[3];
 #pragma unroll
-    for (int f = 0; f < 3; ++f) {
-        const int64_t of = (int64_t)f * L.stride + o;
-        pv[f] = __ldg(p + of); xv[f] = X[of]; rv[f] = R[of]; qv[f] = __ldg(Q + of);
-    }
+        for (int f = 0; f < 3; ++f) {
+            const int64_t of = (int64_t)f * L.stride + o;
+            pv[f] = __ldg(p + of); xv[f] = X[of]; rv[f] = R[of]; qv[f] = __ldg(Q + of);
+        }
 #pragma unroll
-    for (int f = 0; f < 3; ++f) {
-        const int64_t of = (int64_t)f * L.stride + o;
-        X[of] = xv[f] + alpha * pv[f];
-        R[of] = rv[f] - alpha * qv[f];
+        for (int f = 0; f < 3; ++f) {
+            const int64_t of = (int64_t)f * L.stride + o;
+            X[of] = xv[f] + alpha * pv[f];
+            R[of] = rv[f] - alpha * qv[f];
+        }
     }
 }
 

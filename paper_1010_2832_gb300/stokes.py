@@ -53,7 +53,7 @@ EXPORTED = ("stokes_create", "stokes_destroy", "stokes_last_error", "stokes_buil
             "stokes_net_gradient", "stokes_net_train_step", "stokes_set_learned_preconditioner",
             "stokes_learned_grid", "stokes_learned_features", "stokes_learned_targets",
             "stokes_learned_jacobi_steps", "stokes_apply_preconditioner", "stokes_schwarz_setup_ms",
-            "stokes_apply_schwarz_noalloc")
+            "stokes_apply_schwarz_noalloc", "stokes_bench_schwarz_kernels")
 
 
 class BatchIO(C.Structure):
@@ -114,6 +114,7 @@ def load_library(path=LIB_PATH):
         "stokes_apply_preconditioner": (I, [P, I, P, P]),
         "stokes_schwarz_setup_ms": (D, [P]),
         "stokes_apply_schwarz_noalloc": (I, [P, P, P]),
+        "stokes_bench_schwarz_kernels": (I, [P, I, C.POINTER(D), C.POINTER(D), C.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -261,6 +262,13 @@ class StokesContext:
         a, u = C.c_double(), C.c_double()
         self._check(self.lib.stokes_bench_cg_kernels(self.h, precision, launches, C.byref(a), C.byref(u)))
         return a.value, u.value
+
+    def bench_schwarz_kernels(self, launches=50):
+        """Mean device ms of the Schwarz local solves and of the gather, and the
+        local solves' algorithmic bytes per launch."""
+        a, g, b = C.c_double(), C.c_double(), C.c_double()
+        self._check(self.lib.stokes_bench_schwarz_kernels(self.h, launches, C.byref(a), C.byref(g), C.byref(b)))
+        return a.value, g.value, b.value
 
     def active_tiles(self):
         return self.lib.stokes_active_tiles(self.h)
