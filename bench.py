@@ -41,7 +41,10 @@ KERNEL_SOURCES = {
 }
 # (workload, mode, kernel) -> (source hash, dram__bytes_read.sum +
 # dram__bytes_write.sum per launch from one ncu capture of the same command)
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("bumps1024", "fp32", "k_schwarz_gemv"): ("f2fdcf24ca4ada35", 437.937536e6),   # profiles/k_schwarz_gemv_bumps1024.md
+    ("bumps1024", "fp32", "k_apply2d"): ("00443ece1ab7fc9c", 17.073536e6),          # profiles/k_apply2d_bumps1024.md
+}
 
 
 def kernel_source_hash(kernel):
