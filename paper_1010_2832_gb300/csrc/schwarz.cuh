@@ -79,40 +79,54 @@ __global__ void k_schwarz_mark(Layout L, DevArrays D, int npx, int npy, int* fla
 // one CTA (256 threads) per active patch.  The local matrix is assembled in
 // FP64 from the FP64 operator coefficients: in FP32 the cancellation between
 // face terms leaves some patch matrices indefinite.  Only the unit-diagonal
-// matrix is rounded to FP32 for the factorisation.  Dynamic smem: the FP64
-// matrix (PMAX^2 doubles, later reused for X), the scaled FP32 matrix
-// (PMAX^2 floats), the diagonal scaling.
-constexpr int SW_SETUP_SMEM = PMAX * PMAX * 8 + PMAX * PMAX * 4 + PMAX * 4;
+// matrix is rounded to FP32 for the factorisation.  Every global load is
+// issued in parallel (activity flags, then the coefficients of the faces
+// touching the patch, staged in shared memory); one warp then accumulates
+// the faces in a fixed order, so the local matrices are reproducible bit for
+// bit.  Dynamic smem: the FP64 matrix (PMAX^2 doubles), whose upper half
+// later holds the scaled FP32 matrix and whose lower half the inverse factor
+// X = L^-1, then the diagonal scaling: about 94 KB, two CTAs per SM.
+constexpr int SW_NFACE = 2 * (PR + 2) * (PR + 2);   // faces of both directions around a patch
+constexpr int SW_SETUP_SMEM = PMAX * PMAX * 8 + PMAX * 4;
 __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, const double* coef, SchwarzPlan P) {
     extern __shared__ __align__(16) double smd[];
     double* Ad = smd;                                        // n x n (row-major, stride PMAX), FP64
-    float* A = reinterpret_cast<float*>(smd + PMAX * PMAX);  // scaled copy, FP32
-    float* sc = A + PMAX * PMAX;                             // 1/sqrt(diag)
-    float* X = reinterpret_cast<float*>(smd);                // L^-1, once Ad is no longer needed
+    float* A = reinterpret_cast<float*>(smd) + PMAX * PMAX;  // upper half: scaled copy, FP32
+    float* X = reinterpret_cast<float*>(smd);                // lower half: L^-1
+    float* sc = reinterpret_cast<float*>(smd + PMAX * PMAX); // 1/sqrt(diag)
     __shared__ short map[PMAX];
-    __shared__ int n_s;
+    __shared__ unsigned ballots[4];
+    __shared__ double dd[PMAX];                              // 1/sqrt(diag) in FP64, 0 if not positive
+    __shared__ double fK[SW_NFACE], fb[SW_NFACE][6];
+    __shared__ short fidx[SW_NFACE][6];
     const int p = blockIdx.x;
     const int I = P.corner[p] & 0xffff, J = P.corner[p] >> 16;
     const int a0 = PB * I - 1, b0 = PB * J - 1;       // ring origin (slot coords)
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int64_t S = L.stride;
     const double *a_c = coef, *a_n = coef + S, *d_c = coef + 2 * S, *d_n = coef + 3 * S, *K_u = coef + 4 * S,
                  *K_v = coef + 5 * S;
-    // 1. local indices in fixed order (thread 0: 108 positions)
-    if (t == 0) {
-        int n = 0;
-        for (int f = 0; f < 3; ++f)
-            for (int jj = 0; jj < PR; ++jj)
-                for (int ii = 0; ii < PR; ++ii) {
-                    int pos = (f * PR + jj) * PR + ii;
-                    map[pos] = unknown_active(D, L, f, a0 + ii, b0 + jj) ? (short)n++ : (short)-1;
-                }
-        n_s = n;
-        P.nloc[p] = n;
+    // 1. local indices in fixed order (field, row, column): a ballot scan
+    bool act = false;
+    if (t < PMAX) {
+        const int f = t / (PR * PR), rem = t % (PR * PR), jj = rem / PR, ii = rem % PR;
+        act = unknown_active(D, L, f, a0 + ii, b0 + jj);
+    }
+    if (w < 4) {
+        const unsigned m = __ballot_sync(0xffffffffu, act);
+        if (lane == 0) ballots[w] = m;
     }
     __syncthreads();
-    const int n = n_s;
-    for (int e = t; e < PMAX; e += 256) P.lmap[(int64_t)p * PMAX + e] = map[e];
+    int n = 0;
+    for (int q = 0; q < 4; ++q) n += __popc(ballots[q]);
+    if (t < PMAX) {
+        int before = 0;
+        for (int q = 0; q < w; ++q) before += __popc(ballots[q]);
+        before += __popc(ballots[w] & ((1u << lane) - 1u));
+        map[t] = act ? (short)before : (short)-1;
+        P.lmap[(int64_t)p * PMAX + t] = map[t];
+    }
+    if (t == 0) P.nloc[p] = n;
     for (int e = t; e < n * PMAX; e += 256) Ad[e] = 0.0;
     __syncthreads();
     auto lidx = [&](int f, int i, int j) -> int {
@@ -120,7 +134,41 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
         if (ii < 0 || jj < 0 || ii >= PR || jj >= PR) return -1;
         return map[(f * PR + jj) * PR + ii];
     };
-    // 2. stress diagonal C
+    // 2. stage the faces touching the patch (u faces, then v faces; rows
+    // b0-1 .. b0+PR, columns a0-1 .. a0+PR): K, the six coefficients of
+    // B^T's row and the local indices they multiply; K = 0 marks no face
+    if (t < SW_NFACE) {
+        const int dir = t / ((PR + 2) * (PR + 2)), rem = t % ((PR + 2) * (PR + 2));
+        const int i = a0 + rem % (PR + 2) - 1, j = b0 + rem / (PR + 2) - 1;
+        const bool ok = dir == 0 ? (i >= 0 && i <= L.nx && j >= 0 && j < L.ny)
+                                 : (i >= 0 && i < L.nx && j >= 0 && j <= L.ny);
+        double K = 0.0;
+        if (ok) {
+            const int64_t o = L.off(i + 1, j + 1, 0);
+            K = (dir == 0 ? K_u : K_v)[o];
+            if (K != 0.0) {
+                if (dir == 0) {
+                    const double am = a_c[L.off(i, j + 1, 0)], ap = a_c[o];
+                    fidx[t][0] = lidx(0, i - 1, j); fb[t][0] = am;       // txx(i-1): +a
+                    fidx[t][1] = lidx(2, i - 1, j); fb[t][1] = -am;      // p(i-1):   -a
+                    fidx[t][2] = lidx(0, i, j);     fb[t][2] = -ap;      // txx(i):   -a
+                    fidx[t][3] = lidx(2, i, j);     fb[t][3] = ap;       // p(i):     +a
+                    fidx[t][4] = lidx(1, i, j);     fb[t][4] = a_n[o];                     // txy(i, j)
+                    fidx[t][5] = lidx(1, i, j + 1); fb[t][5] = -a_n[L.off(i + 1, j + 2, 0)];  // txy(i, j+1)
+                } else {
+                    const double am = a_c[L.off(i + 1, j, 0)], ap = a_c[o];
+                    fidx[t][0] = lidx(0, i, j - 1); fb[t][0] = -am;      // txx(j-1): -a
+                    fidx[t][1] = lidx(2, i, j - 1); fb[t][1] = -am;      // p(j-1):   -a
+                    fidx[t][2] = lidx(0, i, j);     fb[t][2] = ap;       // txx(j):   +a
+                    fidx[t][3] = lidx(2, i, j);     fb[t][3] = ap;       // p(j):     +a
+                    fidx[t][4] = lidx(1, i, j);     fb[t][4] = a_n[o];                     // txy(i, j)
+                    fidx[t][5] = lidx(1, i + 1, j); fb[t][5] = -a_n[L.off(i + 2, j + 1, 0)];  // txy(i+1, j)
+                }
+            }
+        }
+        fK[t] = K;
+    }
+    // 3. stress diagonal C
     for (int e = t; e < 2 * PR * PR; e += 256) {
         int f = e / (PR * PR), rem = e % (PR * PR), jj = rem / PR, ii = rem % PR;
         int k = map[(f * PR + jj) * PR + ii];
@@ -130,49 +178,22 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
         }
     }
     __syncthreads();
-    // faces touching the patch, one warp, faces in a fixed order; lanes own
+    // 4. K_f beta_f beta_f^T of every face, one warp, faces in order; lanes own
     // distinct (row, column) pairs of one face's 6x6 outer product
     if (t < 32) {
-        for (int dir = 0; dir < 2; ++dir) {
-            // u faces i in [a0+1, a0+PR], j in [b0-1, b0+PR-1]; v faces transposed
-            for (int jj = -1; jj <= PR; ++jj)
-                for (int ii = -1; ii <= PR; ++ii) {
-                    int i = a0 + ii, j = b0 + jj;
-                    int ku_ok = dir == 0 ? (i >= 0 && i <= L.nx && j >= 0 && j < L.ny)
-                                         : (i >= 0 && i < L.nx && j >= 0 && j <= L.ny);
-                    if (!ku_ok) continue;
-                    int64_t o = L.off(i + 1, j + 1, 0);
-                    double K = (dir == 0 ? K_u : K_v)[o];
-                    if (K == 0.0) continue;
-                    int idx[6];
-                    double b[6];
-                    if (dir == 0) {
-                        double am = a_c[L.off(i, j + 1, 0)], ap = a_c[o];
-                        idx[0] = lidx(0, i - 1, j); b[0] = am;       // txx(i-1): +a
-                        idx[1] = lidx(2, i - 1, j); b[1] = -am;      // p(i-1):   -a
-                        idx[2] = lidx(0, i, j);     b[2] = -ap;      // txx(i):   -a
-                        idx[3] = lidx(2, i, j);     b[3] = ap;       // p(i):     +a
-                        idx[4] = lidx(1, i, j);     b[4] = a_n[o];                     // txy(i, j)
-                        idx[5] = lidx(1, i, j + 1); b[5] = -a_n[L.off(i + 1, j + 2, 0)];  // txy(i, j+1)
-                    } else {
-                        double am = a_c[L.off(i + 1, j, 0)], ap = a_c[o];
-                        idx[0] = lidx(0, i, j - 1); b[0] = -am;      // txx(j-1): -a
-                        idx[1] = lidx(2, i, j - 1); b[1] = -am;      // p(j-1):   -a
-                        idx[2] = lidx(0, i, j);     b[2] = ap;       // txx(j):   +a
-                        idx[3] = lidx(2, i, j);     b[3] = ap;       // p(j):     +a
-                        idx[4] = lidx(1, i, j);     b[4] = a_n[o];                     // txy(i, j)
-                        idx[5] = lidx(1, i + 1, j); b[5] = -a_n[L.off(i + 2, j + 1, 0)];  // txy(i+1, j)
-                    }
-                    for (int q = t; q < 36; q += 32) {
-                        int r = q / 6, c = q % 6;
-                        if (idx[r] >= 0 && idx[c] >= 0) Ad[idx[r] * PMAX + idx[c]] += K * b[r] * b[c];
-                    }
-                    __syncwarp();
-                }
+        for (int f = 0; f < SW_NFACE; ++f) {
+            const double K = fK[f];
+            if (K == 0.0) continue;
+            for (int q = t; q < 36; q += 32) {
+                const int r = q / 6, c = q % 6;
+                const int ir = fidx[f][r], ic = fidx[f][c];
+                if (ir >= 0 && ic >= 0) Ad[ir * PMAX + ic] += K * fb[f][r] * fb[f][c];
+            }
+            __syncwarp();
         }
     }
     __syncthreads();
-    // 3. Q A_p Q with Q the symmetric orthogonal pair rotation (rows, then columns)
+    // 5. Q A_p Q with Q the symmetric orthogonal pair rotation (rows, then columns)
     constexpr double H = 0.70710678118654752440;
     for (int e = t; e < PR * PR * n; e += 256) {
         int cell = e / n, c = e % n;
@@ -192,20 +213,38 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
         Ad[r * PMAX + kp] = (a - b) * H;
     }
     __syncthreads();
-    // 4. unit-diagonal scaling (FP64, then rounded), Cholesky (lower, in
-    // place, FP32), inverse of the factor
+    // 6. unit-diagonal scaling (FP64, then rounded to FP32).  The FP32 row r
+    // lands on FP64 rows >= r of the same buffer, so rows are converted from
+    // the last down, a block of rows at a time (read all, barrier, write all).
+    // (FP64 divisions and square roots are slow on this part: one per row)
     for (int k = t; k < n; k += 256) {
-        double d = Ad[k * PMAX + k];
-        sc[k] = d > 0.0 ? (float)(1.0 / sqrt(d)) : 1.f;
+        const double d = Ad[k * PMAX + k];
+        dd[k] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+        sc[k] = d > 0.0 ? (float)dd[k] : 1.f;
     }
     __syncthreads();
-    for (int e = t; e < n * n; e += 256) {
-        int r = e / n, c = e % n;
-        double dr = Ad[r * PMAX + r], dc = Ad[c * PMAX + c];
-        double v = Ad[r * PMAX + c];
-        A[r * PMAX + c] = (dr > 0.0 && dc > 0.0) ? (float)(v / sqrt(dr * dc)) : (r == c ? 1.f : 0.f);
+    constexpr int CONV_ROWS = 16;
+    for (int r1 = n; r1 > 0; r1 -= CONV_ROWS) {
+        const int r0 = max(r1 - CONV_ROWS, 0);
+        float v[(CONV_ROWS * PMAX + 255) / 256];
+#pragma unroll
+        for (int q = 0; q < (CONV_ROWS * PMAX + 255) / 256; ++q) {
+            const int e = t + 256 * q, r = r0 + e / PMAX, c = e % PMAX;
+            v[q] = 0.f;
+            if (r < r1 && c < n) {
+                const double sr = dd[r], scc = dd[c];
+                v[q] = (sr > 0.0 && scc > 0.0) ? (float)(Ad[r * PMAX + c] * sr * scc) : (r == c ? 1.f : 0.f);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < (CONV_ROWS * PMAX + 255) / 256; ++q) {
+            const int e = t + 256 * q, r = r0 + e / PMAX, c = e % PMAX;
+            if (r < r1 && c < n) A[r * PMAX + c] = v[q];
+        }
+        __syncthreads();
     }
-    __syncthreads();
+    // 7. Cholesky (lower, in place, FP32)
     for (int k = 0; k < n; ++k) {
         if (t == 0) {
             float d = A[k * PMAX + k];
@@ -222,18 +261,29 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
         }
         __syncthreads();
     }
-    // X = L^-1, column c by thread c (forward substitution on e_c)
-    for (int c = t; c < n; c += 256) {
-        for (int r = c; r < n; ++r) {
-            float s = r == c ? 1.f : 0.f;
-            for (int q = c; q < r; ++q) s -= A[r * PMAX + q] * X[q * PMAX + c];
-            X[r * PMAX + c] = s / A[r * PMAX + r];
-        }
+    // 8. X = L^-1 by forward elimination on the identity, all columns at
+    // once: row k is final once divided by L_kk, then eliminated from the
+    // rows below (every step parallel over the rows and columns it touches)
+    for (int e = t; e < n * n; e += 256) {
+        const int r = e / n, c = e % n;
+        X[r * PMAX + c] = r == c ? 1.f : 0.f;
     }
     __syncthreads();
-    // packed rows of X (row r: X[r][0..r]) and the scaling.  The patch
-    // operator D^-1/2 X^T X D^-1/2 is symmetric positive definite whatever
-    // the rounding of X (X stays triangular with a positive diagonal).
+    for (int k = 0; k < n; ++k) {
+        const float inv = 1.f / A[k * PMAX + k];
+        for (int c = t; c <= k; c += 256) X[k * PMAX + c] *= inv;
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int e = t; e < m * (k + 1); e += 256) {
+            const int r = k + 1 + e / (k + 1), c = e % (k + 1);
+            X[r * PMAX + c] -= A[r * PMAX + k] * X[k * PMAX + c];
+        }
+        __syncthreads();
+    }
+    // packed rows of X (row r: X[r][0..r], padded to 16 bytes) and the
+    // scaling by position.  The patch operator D^-1/2 X^T X D^-1/2 is
+    // symmetric positive definite whatever the rounding of X (X stays
+    // triangular with a positive diagonal).
     const int n4 = (n + 3) / 4 * 4;
     for (int e = t; e < n * n4; e += 256) {
         int r = e / n4, c = e % n4;
