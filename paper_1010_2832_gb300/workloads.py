@@ -113,6 +113,37 @@ def disk_in_box(n=32, seed=1, radius=0.3):
                  lambda P: 1.0, lambda P: 1.0, lambda d, P: 0.0, ustar)
 
 
+def _smooth_ustar(d, P):
+    """A smooth, non-rigid intermediate velocity (not a solution of anything)."""
+    x, y = P[0], P[1]
+    return np.sin(1.0 + 2.0 * x + 3.0 * y + d) + 0.5 * np.cos(3.0 * x - 2.0 * y + 2.0 * d)
+
+
+def paper_disk(n):
+    """Geometry of Section 9's solver-iteration test with a free surface:
+    n x n grid on [-1, 1]^2 with walls, a liquid disk of radius 0.75 at the
+    origin surrounded by air, rho = 1, mu = 0.1, dt = 1; smooth u*."""
+    h = 2.0 / n
+    lo, hi = (-1.0, -1.0), (1.0, 1.0)
+    return from_functions(f"paperdisk{n}", 2, (n, n), h, 1.0, lo,
+                          lambda X: np.hypot(X[0], X[1]) - 0.75, lambda X: box_phi(X, lo, hi),
+                          lambda P: 1.0, lambda P: 0.1, lambda d, P: 0.0, _smooth_ustar)
+
+
+def paper_annulus(n):
+    """Geometry of Section 9's solver-iteration test with solid walls: n x n
+    grid on [-1, 1]^2, liquid filling the annulus 0.5 <= r <= 1 between two
+    static solid walls, rho = 1, mu = 0.1, dt = 1; smooth u*."""
+    h = 2.0 / n
+    lo, hi = (-1.0, -1.0), (1.0, 1.0)
+    def phiS(X):
+        r = np.hypot(X[0], X[1])
+        return np.minimum(np.minimum(r - 0.5, 1.0 - r), box_phi(X, lo, hi))
+    return from_functions(f"paperannulus{n}", 2, (n, n), h, 1.0, lo,
+                          lambda X: -np.ones(X[0].shape), phiS,
+                          lambda P: 1.0, lambda P: 0.1, lambda d, P: 0.0, _smooth_ustar)
+
+
 def _bumps(rng, dim, k=8, c_lo=0.2, c_hi=0.8, s_lo=0.05, s_hi=0.12):
     c = rng.uniform(c_lo, c_hi, (k, dim))
     s = rng.uniform(s_lo, s_hi, k)

@@ -34,6 +34,8 @@ def _cases():
         "rand3d_b": lambda: W.random_small((20, 17, 9), seed=4, dim=3),
         "column3d": lambda: W.column_3d(24),
         "bumps3d": lambda: W.bumps_3d(20, seed=7),
+        "paper_disk40": lambda: W.paper_disk(40),
+        "paper_annulus48": lambda: W.paper_annulus(48),
     }
 
 
