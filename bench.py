@@ -118,6 +118,7 @@ WORKLOADS = {
                            "mu log-uniform 1e-2..1e2, rho 1|1000, dt=0.01, tol 1e-8", dim=2),
     "column256": dict(desc="3D 256^3 liquid column r=0.05 on a solid floor, rho=1000, mu=10, dt=1e-3, tol 1e-8",
                       dim=3),
+    "column128": dict(desc="the 3D column workload at 128^3 (a small case for profiler captures)", dim=3),
     "batch64": dict(desc="64 independent 2D instances, n ~ U{64..512}, Gaussian-bump liquid, random moving disk, "
                          "mu log-uniform 1e-2..1e2, rho=1, each to 1e-8, one persistent launch under a CUDA graph",
                     dim=2),
@@ -195,6 +196,8 @@ def make_workload(name, rank):
         return W.bumps_2d(1024, seed=2 + rank)
     if name == "column256":
         return W.column_3d(256)
+    if name == "column128":
+        return W.column_3d(128)
     raise SystemExit(f"unknown workload {name}")
 
 

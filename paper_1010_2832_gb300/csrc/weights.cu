@@ -16,14 +16,30 @@ namespace stk {
 //             k=2: [x^2y^2 - (p+q)xy(x+y) + pq(x^2+xy+y^2)] / [(x-p)(x-q)(y-p)(y-q)]
 // (the two-negative tetrahedron written without cancellation).
 // ---------------------------------------------------------------------------
+// Sign tests and ordering on the IEEE bit patterns (integer ALU; FP64
+// compares and min/max run on the FP64 pipe, which is slow on this part).
+// For finite values they decide exactly as v < 0, v > 0 and <= do
+// (-0 is neither negative nor positive and orders with +0).
+__device__ __forceinline__ bool dneg(double v) {
+    const long long b = __double_as_longlong(v);
+    return b < 0 && b != (long long)0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool dpos(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ long long dkey(double v) {
+    const long long b = __double_as_longlong(v);
+    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
 __device__ __forceinline__ void cswap(double& a, double& b) {
-    double lo = fmin(a, b), hi = fmax(a, b);
-    a = lo; b = hi;
+    if (dkey(b) < dkey(a)) {
+        const double t = a;
+        a = b;
+        b = t;
+    }
 }
 
 __device__ double tri_frac(double a, double b, double c) {
     cswap(a, b); cswap(b, c); cswap(a, b);
-    int k = (a < 0) + (b < 0) + (c < 0);
+    int k = dneg(a) + dneg(b) + dneg(c);
     if (k == 0) return 0.0;
     if (k == 3) return 1.0;
     if (k == 1) return __dmul_rn(a, a) / __dmul_rn(__dsub_rn(a, b), __dsub_rn(a, c));
@@ -32,7 +48,7 @@ __device__ double tri_frac(double a, double b, double c) {
 
 __device__ double tet_frac(double a, double b, double c, double d) {
     cswap(a, b); cswap(c, d); cswap(a, c); cswap(b, d); cswap(b, c);
-    int k = (a < 0) + (b < 0) + (c < 0) + (d < 0);
+    int k = dneg(a) + dneg(b) + dneg(c) + dneg(d);
     if (k == 0) return 0.0;
     if (k == 4) return 1.0;
     if (k == 1) {
@@ -74,10 +90,10 @@ __device__ double cv_frac_2d(const double* phi, int Lx, int a, int b) {
     const int da[8] = {1, 1, 0, -1, -1, -1, 0, 1};
     const int db[8] = {0, 1, 1, 1, 0, -1, -1, -1};
     double c = phi[(int64_t)b * Lx + a];
-    int neg = c < 0, pos = c > 0;
+    int neg = dneg(c), pos = dpos(c);
     for (int t = 0; t < 8; ++t) {
         v[t] = phi[(int64_t)(b + db[t]) * Lx + (a + da[t])];
-        neg |= v[t] < 0; pos |= v[t] > 0;
+        neg |= dneg(v[t]); pos |= dpos(v[t]);
     }
     (void)n;
     if (!neg) return 0.0;
@@ -100,7 +116,7 @@ __device__ double cv_frac_3d(const double* phi, int Lx, int Ly, int a, int b, in
         for (int db = -1; db <= 1; ++db)
             for (int da = -1; da <= 1; ++da) {
                 double v = P(da, db, dc);
-                neg |= v < 0; pos |= v > 0;
+                neg |= dneg(v); pos |= dpos(v);
             }
     if (!neg) return 0.0;
     if (!pos) return 1.0;
@@ -154,32 +170,134 @@ __host__ __device__ __forceinline__ bool exists3(int kind, int i, int j, int k, 
 }
 
 // ---- kernel 1: fractions ----------------------------------------------------
+// 2D form of block_sign3: the block [2i, 2i+3]^2, clipped to the lattice.
+__device__ __forceinline__ int block_sign2(const double* phi, int Lx, int Ly, int i, int j) {
+    int neg = 0, nonneg = 0;
+    const int ea = min(4, Lx - 2 * i), eb = min(4, Ly - 2 * j);
+    for (int db = 0; db < eb; ++db)
+        for (int da = 0; da < ea; ++da) {
+            const int n = dneg(phi[(int64_t)(2 * j + db) * Lx + (2 * i + da)]);
+            neg |= n;
+            nonneg |= !n;
+        }
+    return !neg ? 0 : (!nonneg ? 1 : -1);
+}
+
 __global__ void k_fractions2d(Layout L, const double* phiL, const double* phiS, DevArrays D) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i > L.nx || j > L.ny) return;
-    int Lx = 2 * L.nx + 3;
+    int Lx = 2 * L.nx + 3, Ly = 2 * L.ny + 3;
     int64_t o = L.off(i + 1, j + 1, 0);
+    const int bl = block_sign2(phiL, Lx, Ly, i, j), bs = block_sign2(phiS, Lx, Ly, i, j);
     for (int kd = 0; kd < 4; ++kd) {
         if (!exists2(kd, i, j, L.nx, L.ny)) continue;
         int a = 2 * i + c_off2[kd][0], b = 2 * j + c_off2[kd][1];
-        D.WL[kd][o] = cv_frac_2d(phiL, Lx, a, b);
-        D.WF[kd][o] = 1.0 - cv_frac_2d(phiS, Lx, a, b);
+        D.WL[kd][o] = bl >= 0 ? (double)bl : cv_frac_2d(phiL, Lx, a, b);
+        D.WF[kd][o] = bs >= 0 ? 1.0 - (double)bs : 1.0 - cv_frac_2d(phiS, Lx, a, b);
     }
 }
 
+// Sign summary of the lattice block [2i, 2i+3]^3 (clipped to the lattice,
+// whose last index per axis is 2n+2) that holds the control volumes of all
+// seven sample kinds of slot (i, j, k) that exist (at i = nx only kinds
+// centred at 2i+1 exist, and their points end at 2nx+2): 0 if the block has
+// no negative value (every fraction is 0), 1 if every value is negative
+// (every fraction is 1), -1 otherwise (evaluate each kind).
+__device__ __forceinline__ int block_sign3(const double* phi, int Lx, int Ly, int Lz, int i, int j, int k) {
+    int neg = 0, nonneg = 0;
+    const int ea = min(4, Lx - 2 * i), eb = min(4, Ly - 2 * j), ec = min(4, Lz - 2 * k);
+    for (int dc = 0; dc < ec; ++dc)
+        for (int db = 0; db < eb; ++db)
+            for (int da = 0; da < ea; ++da) {
+                const double v = phi[((int64_t)(2 * k + dc) * Ly + (2 * j + db)) * Lx + (2 * i + da)];
+                const int n = dneg(v);
+                neg |= n;
+                nonneg |= !n;
+            }
+    return !neg ? 0 : (!nonneg ? 1 : -1);
+}
+
+// Fraction of the CV centred at lattice (a, b, c) computed by a whole warp
+// (every lane must call it with the same arguments): lanes 0..26 test the 27
+// lattice values for one sign; otherwise lane l < 24 evaluates tetrahedron l
+// (faces -x, +x, -y, +y, -z, +z, four per face, as in cv_frac_3d) and the 24
+// values are added in that order, so the result is cv_frac_3d's bit for bit.
+__device__ double cv_frac_3d_warp(const double* phi, int Lx, int Ly, int a, int b, int c) {
+    const int lane = threadIdx.x & 31;
+    auto P = [&](int da, int db, int dc) -> double {
+        return phi[((int64_t)(c + dc) * Ly + (b + db)) * Lx + (a + da)];
+    };
+    int isneg = 0, ispos = 0;
+    if (lane < 27) {
+        const double v = P(lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1);
+        isneg = dneg(v);
+        ispos = dpos(v);
+    }
+    const unsigned neg = __ballot_sync(0xffffffffu, isneg), pos = __ballot_sync(0xffffffffu, ispos);
+    if (!neg) return 0.0;
+    if (!pos) return 1.0;
+    double tv = 0.0;
+    if (lane < 24) {
+        const int face = lane >> 2, t = lane & 3;
+        const int axis = face >> 1, sg = (face & 1) ? 1 : -1;
+        int o[3] = {0, 0, 0};
+        o[axis] = sg;
+        const int ua = axis == 0 ? 1 : 0, va = axis == 2 ? 1 : 2;
+        const int lu[4] = {-1, 1, 1, -1}, lv[4] = {-1, -1, 1, 1};
+        int q0[3] = {o[0], o[1], o[2]}, q1[3] = {o[0], o[1], o[2]};
+        q0[ua] = lu[t]; q0[va] = lv[t];
+        q1[ua] = lu[(t + 1) & 3]; q1[va] = lv[(t + 1) & 3];
+        tv = tet_frac(P(0, 0, 0), P(o[0], o[1], o[2]), P(q0[0], q0[1], q0[2]), P(q1[0], q1[1], q1[2]));
+    }
+    double sum = 0.0;
+    for (int l = 0; l < 24; ++l) sum += __shfl_sync(0xffffffffu, tv, l);
+    return clamp_open(sum / 24.0);
+}
+
+// One thread per slot decides, from a sign scan of its lattice block, which
+// of its fractions are 0 or 1 outright; the control volumes cut by an
+// interface are then evaluated by the whole warp, one at a time (the
+// interfaces are thin, so most warps hold few of them, and a serial
+// per-thread evaluation would leave the other lanes idle on the slow FP64
+// pipe).
 __global__ void k_fractions3d(Layout L, const double* phiL, const double* phiS, DevArrays D) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
     int k = blockIdx.z;
-    if (i > L.nx || j > L.ny || k > L.nz) return;
-    int Lx = 2 * L.nx + 3, Ly = 2 * L.ny + 3;
-    int64_t o = L.off(i + 1, j + 1, k + 1);
-    for (int kd = 0; kd < 7; ++kd) {
-        if (!exists3(kd, i, j, k, L.nx, L.ny, L.nz)) continue;
-        int a = 2 * i + c_off3[kd][0], b = 2 * j + c_off3[kd][1], c = 2 * k + c_off3[kd][2];
-        D.WL[kd][o] = cv_frac_3d(phiL, Lx, Ly, a, b, c);
-        D.WF[kd][o] = 1.0 - cv_frac_3d(phiS, Lx, Ly, a, b, c);
+    const bool inside = i <= L.nx && j <= L.ny && k <= L.nz;
+    int Lx = 2 * L.nx + 3, Ly = 2 * L.ny + 3, Lz = 2 * L.nz + 3;
+    int64_t o = inside ? L.off(i + 1, j + 1, k + 1) : 0;
+    unsigned need = 0;                          // bit kd: W_L of kind kd, bit 7 + kd: W_F
+    if (inside) {
+        // the seven CVs lie in a 4x4x4 block of the (padded) lattice: one
+        // sign scan of it settles every kind away from the interfaces
+        const int bl = block_sign3(phiL, Lx, Ly, Lz, i, j, k), bs = block_sign3(phiS, Lx, Ly, Lz, i, j, k);
+        for (int kd = 0; kd < 7; ++kd) {
+            if (!exists3(kd, i, j, k, L.nx, L.ny, L.nz)) continue;
+            if (bl >= 0) D.WL[kd][o] = (double)bl; else need |= 1u << kd;
+            if (bs >= 0) D.WF[kd][o] = 1.0 - (double)bs; else need |= 1u << (7 + kd);
+        }
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, need != 0);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const unsigned nd = __shfl_sync(0xffffffffu, need, src);
+        const int si = __shfl_sync(0xffffffffu, i, src), sj = __shfl_sync(0xffffffffu, j, src);
+        const long long so = __shfl_sync(0xffffffffu, (long long)o, src);
+        for (int bit = 0; bit < 14; ++bit) {
+            if (!(nd & (1u << bit))) continue;
+            const int kd = bit % 7;
+            const int a = 2 * si + c_off3[kd][0], b = 2 * sj + c_off3[kd][1], c = 2 * k + c_off3[kd][2];
+            if (bit < 7) {
+                const double f = cv_frac_3d_warp(phiL, Lx, Ly, a, b, c);
+                if ((threadIdx.x & 31) == src) D.WL[kd][so] = f;
+            } else {
+                const double f = cv_frac_3d_warp(phiS, Lx, Ly, a, b, c);
+                if ((threadIdx.x & 31) == src) D.WF[kd][so] = 1.0 - f;
+            }
+        }
     }
 }
 
