@@ -127,8 +127,10 @@ WORKLOADS = {
 
 def run_batched(args, rank, world):
     """Config-4 step: weights of all instances, then one batched step
-    (right-hand sides, persistent FP64 Jacobi-PCG of every instance, recovery)
-    replayed from a CUDA graph.  Baseline: the same instances one by one."""
+    (right-hand sides, the Schwarz setup of every instance, persistent FP64
+    PCG of every instance with the additive Schwarz preconditioner (or
+    Jacobi), recovery) replayed from a CUDA graph.  Baseline: the same
+    instances one by one with plain FP64 Jacobi-PCG."""
     import torch
     from paper_1010_2832_gb300 import stokes, workloads as W
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -137,7 +139,8 @@ def run_batched(args, rank, world):
     made = [stokes.context_for(wl) for wl in wls]
     ctxs = [m[0] for m in made]
     devs = [m[1] for m in made]
-    opt = stokes.default_options(mode=0, tol=args.tol)
+    precond = 2 if args.precond == "schwarz" else 0
+    opt = stokes.default_options(mode=0, tol=args.tol, precond=precond)
     t0 = time.perf_counter()
     batch = stokes.Batch(ctxs, opt)
     tune_s = time.perf_counter() - t0
@@ -166,10 +169,11 @@ def run_batched(args, rank, world):
             torch.cuda.synchronize()
             times.append(ev0.elapsed_time(ev1))
     ms_step = float(np.mean(times))
-    # baseline: the same instances one at a time (FP64 Jacobi-PCG, graph loop)
+    # baseline: the same instances one at a time (plain FP64 Jacobi-PCG, graph loop)
     seq_ms, seq_iters = 0.0, []
+    opt_plain = stokes.default_options(mode=0, tol=args.tol, precond=0)
     for (c, d), wl, oo in zip(zip(ctxs, devs), wls, o):
-        st = c.solve_step(d["u_star"], oo[0], oo[1], oo[2], opt)
+        st = c.solve_step(d["u_star"], oo[0], oo[1], oo[2], opt_plain)
         seq_ms += st.ms_rhs + st.ms_solve + st.ms_recover
         seq_iters.append(st.iterations)
     tun = batch.tuning()
@@ -179,6 +183,7 @@ def run_batched(args, rank, world):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded)",
         "config": {"workload": "batch64", "desc": WORKLOADS["batch64"]["desc"],
+                   "preconditioner": ["jacobi", "learned", "schwarz"][precond],
                    "sizes": [wl.n[0] for wl in wls], "l2": "inputs 64 instances (> L2 in total)"},
         "batched": {"ms_batched_solve": float(ms), "tuning": tun, "tuning_s": tune_s,
                     "iterations_max": max(s["iterations"] for s in stats),
@@ -239,9 +244,16 @@ def run_ours(args, rank, world):
                                  use_graph=0 if args.no_graph else 1, precond=precond)
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device=dev)
 
+    wev0, wev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    weights_ms = []
+
     def step():
-        ctx.build_weights(d["phi_liquid"], d["phi_solid"], d["rho"], d["mu"], d["u_bc"])
-        return ctx.solve_step(d["u_star"], u_out, taus, p, opt)
+        wev0.record()
+        ctx.build_weights(d["phi_liquid"], d["phi_solid"], d["rho"], d["mu"], d["u_bc"])   # synchronises
+        wev1.record()
+        st = ctx.solve_step(d["u_star"], u_out, taus, p, opt)
+        weights_ms.append(wev0.elapsed_time(wev1))
+        return st
 
     for _ in range(args.warmup):
         st = step()
@@ -249,6 +261,7 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     times, stats = [], []
+    weights_ms.clear()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(dev.index) as clk:
         for k in range(args.steps):
@@ -331,7 +344,8 @@ def run_ours(args, rank, world):
                "unit": "GB/s", "frac": apply_gbs / peak, "ms_per_launch": ms_apply, "bytes_per_launch": apply_bytes,
                "update_ms_per_launch": ms_update}
     if not args.no_dense_apply:
-        stencil["dense"] = dense_apply(wl.dim, prec, peak)
+        stencil["dense"] = [dense_apply(dim, n, pr, peak) for dim, n in ((2, 4096), (2, 1024), (3, 256))
+                            for pr in (1, 0, 2)]
     out = {
         "metric": "time-to-solution per implicit step at 1e-8 rel. residual",
         "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -345,6 +359,8 @@ def run_ours(args, rank, world):
                    "failed_steps": len(bad), "ms_rhs": float(np.mean([s["ms_rhs"] for s in stats])),
                    "ms_solve": float(np.mean([s["ms_solve"] for s in stats])),
                    "ms_recover": float(np.mean([s["ms_recover"] for s in stats])),
+                   "ms_weights": float(np.mean(weights_ms[:args.steps])) if weights_ms else None,
+                   "ms_schwarz_setup": ctx.schwarz_setup_ms() if precond == 2 else None,
                    "steps_per_s_all_ranks": world * 1000.0 / ms},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
         "gpu_launches": launches * args.steps,
@@ -355,12 +371,12 @@ def run_ours(args, rank, world):
     return out, wl
 
 
-def dense_apply(dim, prec, peak):
-    """The CG-mode apply on a box full of liquid (2D 4096^2 or 3D 256^3), where
-    every tile is active: the stencil's streaming bandwidth at scale."""
+def dense_apply(dim, n, prec, peak):
+    """The CG-mode apply on an n^dim box full of liquid, where every tile is
+    active: the stencil's streaming bandwidth at scale (precision 0 FP64,
+    1 FP32, 2 BF16 coefficients with FP32 vectors)."""
     import torch
     from paper_1010_2832_gb300 import stokes, workloads as W
-    n = 4096 if dim == 2 else 256
     wl = W.full_box(n, dim)
     ctx, d = stokes.context_for(wl)
     if dim == 2:
@@ -378,9 +394,10 @@ def dense_apply(dim, prec, peak):
     ctx.close()
     del u, taus, p, d
     torch.cuda.empty_cache()
-    return {"workload": f"{dim}D {n}^{dim} box full of liquid", "achieved": gbs, "frac": gbs / peak,
-            "ms_per_launch": ms_a, "bytes_per_launch": by, "units_per_launch": slots,
-            "bytes_per_unit": bytes_per_slot_apply(dim, prec)}
+    return {"workload": f"{dim}D {n}^{dim} box full of liquid", "precision": ["fp64", "fp32", "bf16"][prec],
+            "achieved": gbs, "frac": gbs / peak, "ms_per_launch": ms_a, "bytes_per_launch": by,
+            "units_per_launch": slots, "bytes_per_unit": bytes_per_slot_apply(dim, prec),
+            "update_ms_per_launch": ms_u}
 
 
 def cpu_sample(wl, n_iter_fp64, budget_s=12.0):

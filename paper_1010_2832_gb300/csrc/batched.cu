@@ -2,12 +2,14 @@
 // one per context) in one persistent cooperative kernel.
 //
 // Work list: the active tiles of every instance, concatenated (instance i
-// owns the contiguous range [tb_i, te_i)).  Each CTA walks the list with a
-// grid stride.  Per CG iteration, two phases separated by grid barriers:
+// owns the contiguous range [tb_i, te_i)); with the Schwarz preconditioner
+// also every instance's active patches.  Each CTA walks the lists with a
+// grid stride.  Per CG iteration, phases separated by grid barriers:
 //   A  CG instances: p = z + beta p_old, q = A p, p.q   -> alpha
 //      CHECK instances: r = b - A x (true FP64 residual)
-//   B  CG instances: x += alpha p, r -= alpha q, z = M^-1 r, r.z, r.r
-//      CHECK instances: z = M^-1 r, r.z, r.r of the true residual
+//   C  (Schwarz only) local patch solves on r - alpha q (r in CHECK mode)
+//   D  CG instances: x += alpha p, r -= alpha q; every instance:
+//      z = M^-1 r (Jacobi, or the gather of the local results), r.z, r.r
 // The CTA that reports an instance's last tile of a phase reduces that
 // instance's per-tile partials in list order (deterministic) and updates
 // its scalars: CG -> CHECK when the recurrence residual meets the
@@ -28,8 +30,10 @@
 #include "internal.cuh"
 #include "ctx.cuh"
 #include "apply2d_tile.cuh"
+#include "schwarz_plan.cuh"
 
 namespace stk {
+cudaError_t schwarz_ensure(Ctx* c, const SchwarzPlan** plan);
 cudaError_t launch_rhs(Ctx* c, const double* const* ustar, double* b);
 cudaError_t launch_recover(Ctx* c, const double* const* ustar, const double* x, double* const* uout);
 cudaError_t launch_unpack(Ctx* c, const double* slots, double* const* fields, int to_fields);
@@ -47,11 +51,15 @@ struct BInst {
     double *x, *r, *z, *q;
     double* p[2];
     int tb, te;
+    int use_sw;                     // additive Schwarz preconditioner (else Jacobi)
+    SchwarzPlan sw;
+    const uint8_t* act_cell;
+    const uint8_t* act_node;
 };
 
 struct BState {
     double rz, rr, alpha, beta, tol2, bb;
-    int mode;      // 0 CG, 1 CHECK (true residual)
+    int mode;      // 0 CG, 1 CHECK (true residual), 2 START (Schwarz: first z = M^-1 b pending)
     int parity, iter, done, status;
     unsigned cnt;
 };
@@ -131,25 +139,183 @@ __device__ void tile_report(double v0, double v1, double* part, int w, BState* s
     __syncthreads();
 }
 
-template <int TY>
+// Additive Schwarz local solve of patch p of instance I, by the whole CTA
+// (256 threads; the triangular products use 128): the same arithmetic as
+// the single-system kernel k_schwarz_gemv, on r_eff = r - alpha q read in
+// FP64 (alpha = 0 outside a CG step).  Thread 0 starts the bulk copy of the
+// factor and waits on the CTA's mbarrier (phase parity = uses & 1, bounded);
+// a copy that never completes sets the batch's error flag.
+__device__ void batched_local_solve(const BInst& I, int p, double alpha, float* Xs, float* s, float* y,
+                                    unsigned long long* bar, uint32_t& uses, int& ok_s, BGlobal* g) {
+    const SchwarzPlan& P = I.sw;
+    const Layout& L = I.L;
+    const int t = threadIdx.x;
+    // after an error (a copy that timed out) start no further copies; the
+    // decision is the same for the whole CTA
+    if (t == 0) ok_s = ((volatile int*)&g->err)[0] == 0;
+    __syncthreads();
+    if (!ok_s) return;
+    const int n = P.nloc[p];
+    const uint32_t b_addr = smem_u32(bar);
+    if (t == 0) sw_issue(b_addr, Xs, P.inv + (int64_t)p * PFAC, (uint32_t)(tri4_off(n) * (int)sizeof(float)));
+    constexpr float H = 0.70710678118654752f;
+    const int CI = P.corner[p] & 0xffff, CJ = P.corner[p] >> 16;
+    const int a0 = PB * CI - 1, b0 = PB * CJ - 1;
+    const short* map = P.lmap + (int64_t)p * PMAX;
+    const float* scl = P.scale + (int64_t)p * PMAX;
+    int kk = -1, kp = -1;
+    float sa = 0.f, sb = 0.f;
+    if (t < 2 * PR * PR) {
+        const int e = t;
+        const int rem = e % (PR * PR), jj = rem / PR, ii = rem % PR;
+        const int64_t o = L.off(a0 + ii + 1, b0 + jj + 1, 0);
+        kk = map[e];
+        sa = scl[e];
+        if (e >= PR * PR) {
+            const float rv = (float)(I.r[L.stride + o] - alpha * I.q[L.stride + o]);
+            if (kk >= 0) s[kk] = rv * sa;
+        } else {
+            kp = map[2 * PR * PR + e];
+            sb = scl[2 * PR * PR + e];
+            const float rt = (float)(I.r[o] - alpha * I.q[o]);
+            const float rp = (float)(I.r[2 * L.stride + o] - alpha * I.q[2 * L.stride + o]);
+            if (kk >= 0 && kp >= 0) {
+                s[kk] = (rt + rp) * H * sa;
+                s[kp] = (rt - rp) * H * sb;
+            } else if (kk >= 0) {
+                s[kk] = rt * sa;
+            } else if (kp >= 0) {
+                s[kp] = rp * sb;
+            }
+        }
+    }
+    if (t >= n && t < (n + 3) / 4 * 4) s[t] = 0.f;
+    if (t == 0) {
+        ok_s = mbar_wait(b_addr, uses & 1u) ? 1 : 0;
+        ++uses;
+    }
+    __syncthreads();
+    if (!ok_s) {
+        if (t == 0) {
+            mbar_wait(b_addr, (uses - 1u) & 1u);
+            atomicExch(&g->err, (int)STOKES_ERR_TIMEOUT);
+        }
+        __syncthreads();
+        return;
+    }
+    if (t < n) {
+        const float* xr = Xs + tri4_off(t);
+        const float4* s4 = reinterpret_cast<const float4*>(s);
+        float acc = 0.f;
+        for (int j = 0; j <= t / 4; ++j) {
+            const float4 a = *reinterpret_cast<const float4*>(xr + 4 * j), b = s4[j];
+            acc = fmaf(a.x, b.x, acc);
+            acc = fmaf(a.y, b.y, acc);
+            acc = fmaf(a.z, b.z, acc);
+            acc = fmaf(a.w, b.w, acc);
+        }
+        y[t] = acc;
+    }
+    __syncthreads();
+    {
+        const int cb = t >> 2, q = t & 3;
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (4 * cb < n)
+            for (int row = 4 * cb + q; row < n; row += 4) {
+                const float4 a = *reinterpret_cast<const float4*>(Xs + tri4_off(row) + 4 * cb);
+                const float yr = y[row];
+                z.x = fmaf(a.x, yr, z.x);
+                z.y = fmaf(a.y, yr, z.y);
+                z.z = fmaf(a.z, yr, z.z);
+                z.w = fmaf(a.w, yr, z.w);
+            }
+        for (int o = 1; o <= 2; o <<= 1) {
+            z.x += __shfl_xor_sync(0xffffffffu, z.x, o);
+            z.y += __shfl_xor_sync(0xffffffffu, z.y, o);
+            z.z += __shfl_xor_sync(0xffffffffu, z.z, o);
+            z.w += __shfl_xor_sync(0xffffffffu, z.w, o);
+        }
+        if (q == 0 && 4 * cb < n) reinterpret_cast<float4*>(s)[cb] = z;
+    }
+    __syncthreads();
+    float* out = P.ybuf + (int64_t)(CJ * P.npx + CI) * PMAX;
+    if (t < 2 * PR * PR) {
+        const int e = t;
+        if (e >= PR * PR) {
+            if (kk >= 0) out[e] = s[kk] * sa;
+        } else if (kk >= 0 && kp >= 0) {
+            const float a = s[kk] * sa, b = s[kp] * sb;
+            out[e] = (a + b) * H;
+            out[2 * PR * PR + e] = (a - b) * H;
+        } else if (kk >= 0) {
+            out[e] = s[kk] * sa;
+        } else if (kp >= 0) {
+            out[2 * PR * PR + e] = s[kp] * sb;
+        }
+    }
+    __syncthreads();                             // the next patch reuses shared memory
+}
+
+// z of field f at sample (i, j) from the patches' local results (the
+// single-system gather schwarz_gather_slot, in FP64 out).
+__device__ __forceinline__ double batched_gather(const BInst& I, int f, int i, int j, double r) {
+    const Layout& L = I.L;
+    if (!unknown_active(I.act_cell, I.act_node, L, f, i, j))
+        return (i >= 0 && j >= 0 && i <= L.nx && j <= L.ny) ? r : 0.0;
+    const SchwarzPlan& P = I.sw;
+    const int ilo = max((i + PB - 1) / PB - 1, 0), ihi = min((i + 1) / PB, P.npx - 1);
+    const int jlo = max((j + PB - 1) / PB - 1, 0), jhi = min((j + 1) / PB, P.npy - 1);
+    float s = 0.f;
+    for (int J = jlo; J <= jhi; ++J)
+        for (int Ip = ilo; Ip <= ihi; ++Ip) {
+            const int ii = i - (PB * Ip - 1), jj = j - (PB * J - 1);
+            s += P.ybuf[(int64_t)(J * P.npx + Ip) * PMAX + (f * PR + jj) * PR + ii];
+        }
+    return (double)s;
+}
+
+template <int TY, bool SW>
+struct BatchedSmem {
+    static constexpr int APPLY = (int)sizeof(Smem2<double, TY>);
+    static constexpr int LOCAL = SW ? PFAC * (int)sizeof(float) : 0;
+    static constexpr int BYTES = APPLY > LOCAL ? APPLY : LOCAL;
+};
+
+template <int TY, bool SW>
 __global__ void __launch_bounds__(256) k_batched(const BInst* __restrict__ inst, BState* st,
                                                  const int* __restrict__ wl_inst, const int* __restrict__ wl_c0,
-                                                 const int* __restrict__ wl_r0, int nwork, double* part, BGlobal* g,
-                                                 int ninst, int max_iter, double tol) {
-    __shared__ Smem2<double, TY> sm;
+                                                 const int* __restrict__ wl_r0, int nwork,
+                                                 const int* __restrict__ pl_inst, const int* __restrict__ pl_patch,
+                                                 int npatch, double* part, BGlobal* g, int ninst, int max_iter,
+                                                 double tol) {
+    // shared memory: the apply's staging (phase A) and the local solves'
+    // factor (phase C) never live at the same time
+    __shared__ __align__(128) unsigned char smraw[BatchedSmem<TY, SW>::BYTES];
+    Smem2<double, TY>& sm = *reinterpret_cast<Smem2<double, TY>*>(smraw);
+    float* Xs = reinterpret_cast<float*>(smraw);
+    __shared__ __align__(16) float ls[SW ? PMAX : 4];
+    __shared__ float ly[SW ? PMAX : 4];
+    __shared__ __align__(8) unsigned long long lbar;
+    __shared__ int lok;
+    uint32_t uses = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned nb = gridDim.x;
-    // ---- init: r = b, x = 0, z = M^-1 r, p = 0 ------------------------------
+    if (SW && threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&lbar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // ---- init: r = b, x = 0, p = 0; Jacobi: z = M^-1 r (Schwarz: later) --
     for (int w = blockIdx.x; w < nwork; w += nb) {
         const int i = wl_inst[w];
         const BInst& I = inst[i];
+        const bool swi = SW && I.use_sw;
         const int64_t S = I.L.stride;
         double rz = 0.0, rr = 0.0;
         for (int row = warp; row < TY; row += 8) {
             int64_t o = I.L.off(wl_c0[w] + lane, wl_r0[w] + row, 0);
             for (int f = 0; f < 3; ++f) {
                 int64_t of = f * S + o;
-                double r = I.b[of], z = I.minv[of] * r;
+                double r = I.b[of], z = swi ? 0.0 : I.minv[of] * r;
                 I.r[of] = r; I.z[of] = z; I.x[of] = 0.0; I.p[0][of] = 0.0; I.p[1][of] = 0.0;
                 rz = fma(r, z, rz); rr = fma(r, r, rr);
             }
@@ -157,7 +323,7 @@ __global__ void __launch_bounds__(256) k_batched(const BInst* __restrict__ inst,
         BState* s = st + i;
         tile_report(warp_sum(rz), warp_sum(rr), part, w, s, I, [&](double trz, double trr) {
             s->rz = trz; s->rr = trr; s->bb = trr; s->tol2 = tol * tol * trr;
-            s->mode = 0; s->parity = 0; s->iter = 0; s->beta = 0.0; s->status = 0;
+            s->mode = swi ? 2 : 0; s->parity = 0; s->iter = 0; s->beta = 0.0; s->status = 0; s->alpha = 0.0;
             s->done = trr == 0.0 ? 1 : 0;
             if (!isfinite(trr)) { s->done = 1; s->status = STOKES_ERR_NONFINITE; }
             if (s->done) atomicAdd(&g->ndone, 1);
@@ -166,11 +332,11 @@ __global__ void __launch_bounds__(256) k_batched(const BInst* __restrict__ inst,
     if (!grid_sync(g, nb)) return;
     for (;;) {
         if (((volatile int*)&g->ndone)[0] >= ninst) return;
-        // ---- phase A ---------------------------------------------------------
+        // ---- phase A: CG: p = z + beta p_old, q = A p, p.q; CHECK: r = b - A x
         for (int w = blockIdx.x; w < nwork; w += nb) {
             const int i = wl_inst[w];
             volatile BState* vs = st + i;
-            if (vs->done) continue;
+            if (vs->done || vs->mode == 2) continue;
             const BInst& I = inst[i];
             BState* s = st + i;
             double v;
@@ -195,12 +361,24 @@ __global__ void __launch_bounds__(256) k_batched(const BInst* __restrict__ inst,
             __syncthreads();
         }
         if (!grid_sync(g, nb)) return;
-        // ---- phase B ---------------------------------------------------------
+        // ---- phase C (Schwarz): local solves on r_eff = r - alpha q ----------
+        if (SW) {
+            for (int k = blockIdx.x; k < npatch; k += nb) {
+                const int i = pl_inst[k];
+                volatile BState* vs = st + i;
+                if (vs->done) continue;
+                const double alpha = vs->mode == 0 ? vs->alpha : 0.0;
+                batched_local_solve(inst[i], pl_patch[k], alpha, Xs, ls, ly, &lbar, uses, lok, g);
+            }
+            if (!grid_sync(g, nb)) return;
+        }
+        // ---- phase D: CG: x += alpha p, r -= alpha q; z = M^-1 r; r.z, r.r ---
         for (int w = blockIdx.x; w < nwork; w += nb) {
             const int i = wl_inst[w];
             volatile BState* vs = st + i;
             if (vs->done) continue;
             const BInst& I = inst[i];
+            const bool swi = SW && I.use_sw;
             BState* s = st + i;
             const int64_t S = I.L.stride;
             const int mode = vs->mode;
@@ -208,7 +386,8 @@ __global__ void __launch_bounds__(256) k_batched(const BInst* __restrict__ inst,
             const double* pn = I.p[vs->parity ^ 1];
             double rz = 0.0, rr = 0.0;
             for (int row = warp; row < TY; row += 8) {
-                int64_t o = I.L.off(wl_c0[w] + lane, wl_r0[w] + row, 0);
+                const int c = wl_c0[w] + lane, rw = wl_r0[w] + row;
+                int64_t o = I.L.off(c, rw, 0);
                 for (int f = 0; f < 3; ++f) {
                     int64_t of = f * S + o;
                     double r;
@@ -219,7 +398,7 @@ __global__ void __launch_bounds__(256) k_batched(const BInst* __restrict__ inst,
                     } else {
                         r = I.r[of];
                     }
-                    double z = I.minv[of] * r;
+                    double z = swi ? batched_gather(I, f, c - 1, rw - 1, r) : I.minv[of] * r;
                     I.z[of] = z;
                     rz = fma(r, z, rz); rr = fma(r, r, rr);
                 }
@@ -229,7 +408,13 @@ __global__ void __launch_bounds__(256) k_batched(const BInst* __restrict__ inst,
                 if (!isfinite(trr) || !isfinite(trz)) {
                     s->done = 1; s->status = STOKES_ERR_NONFINITE; atomicAdd(&g->ndone, 1); return;
                 }
-                if (mode == 0) {
+                if (mode == 2) {                           // first preconditioned residual
+                    if (!(trz > 0.0)) {
+                        s->done = 1; s->status = STOKES_ERR_BREAKDOWN; atomicAdd(&g->ndone, 1);
+                    } else {
+                        s->rz = trz; s->mode = 0; s->beta = 0.0;
+                    }
+                } else if (mode == 0) {
                     s->iter += 1;
                     if (trr <= s->tol2) {
                         s->mode = 1;                       // verify with the true residual
@@ -264,6 +449,10 @@ struct stokes_batch_s {
     std::vector<stokes_ctx> ctx;
     std::vector<Ctx*> c;
     int n = 0;
+    bool sw = false;            // additive Schwarz preconditioner for every instance
+    int* d_pl = nullptr;        // [2][pl_cap]: instance, patch
+    int npatch = 0, pl_cap = 0;
+    std::vector<const float*> plan_key;   // each instance's factor pointer when the plan was uploaded
     stokes_options opt{};
     cudaStream_t s = nullptr;
     int ty = 8, cps = 1;        // chosen tile height and CTAs per SM
@@ -293,14 +482,15 @@ static int num_sms() {
     return n;
 }
 
-template <int TY> static void* kernel_ptr() { return (void*)k_batched<TY>; }
-static void* kernel_for(int ty) {
-    return ty == 4 ? kernel_ptr<4>() : ty == 16 ? kernel_ptr<16>() : kernel_ptr<8>();
+template <int TY, bool SW> static void* kernel_ptr() { return (void*)k_batched<TY, SW>; }
+static void* kernel_for(int ty, bool sw) {
+    if (sw) return ty == 4 ? kernel_ptr<4, true>() : ty == 16 ? kernel_ptr<16, true>() : kernel_ptr<8, true>();
+    return ty == 4 ? kernel_ptr<4, false>() : ty == 16 ? kernel_ptr<16, false>() : kernel_ptr<8, false>();
 }
 
-static int max_ctas_per_sm(int ty) {
+static int max_ctas_per_sm(int ty, bool sw) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(ty), 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(ty, sw), 256, 0);
     return nb;
 }
 
@@ -324,6 +514,15 @@ static cudaError_t build_worklist(stokes_batch b, int ty, std::vector<int>& wi, 
         I.x = c->x64;
         I.r = c->w64.r; I.z = c->w64.z; I.q = c->w64.q;
         I.p[0] = c->w64.p[0]; I.p[1] = c->w64.p[1];
+        I.use_sw = b->sw ? 1 : 0;
+        I.act_cell = c->A.act[0];
+        I.act_node = c->A.act[1];
+        std::memset(&I.sw, 0, sizeof(I.sw));
+        if (b->sw) {
+            const SchwarzPlan* P = nullptr;
+            if ((e = schwarz_ensure(c, &P)) != cudaSuccess) return e;
+            I.sw = *P;
+        }
         I.tb = (int)wi.size();
         int per = ty / 4;
         for (int tr = 0; tr < L.R / ty; ++tr)
@@ -333,6 +532,36 @@ static cudaError_t build_worklist(stokes_batch b, int ty, std::vector<int>& wi, 
                 if (a) { wi.push_back(i); wc.push_back(tx * TX); wr.push_back(tr * ty); }
             }
         I.te = (int)wi.size();
+    }
+    return cudaSuccess;
+}
+
+// Patch list of the Schwarz phase (instance, patch), in instance order; a
+// larger list than the last one reallocates (and so needs a new graph).
+static cudaError_t upload_patches(stokes_batch b, const std::vector<BInst>& insts) {
+    b->plan_key.assign(b->n, nullptr);
+    if (!b->sw) { b->npatch = 0; return cudaSuccess; }
+    std::vector<int> pi, pp;
+    for (int i = 0; i < b->n; ++i) {
+        b->plan_key[i] = insts[i].sw.inv;
+        if (insts[i].te == insts[i].tb) continue;        // no active tile: retired at once
+        for (int q = 0; q < insts[i].sw.np; ++q) { pi.push_back(i); pp.push_back(q); }
+    }
+    const int np = (int)pi.size();
+    cudaError_t e;
+    if (np > b->pl_cap || !b->d_pl) {
+        if (b->d_pl) cudaFree(b->d_pl);
+        b->d_pl = nullptr;
+        b->pl_cap = std::max(np, 1);
+        if ((e = cudaMalloc(&b->d_pl, 2 * (size_t)b->pl_cap * sizeof(int))) != cudaSuccess) return e;
+        if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    }
+    if (np != b->npatch && b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    b->npatch = np;
+    if (np) {
+        if ((e = cudaMemcpy(b->d_pl, pi.data(), np * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(b->d_pl + b->pl_cap, pp.data(), np * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
     }
     return cudaSuccess;
 }
@@ -361,6 +590,7 @@ static cudaError_t upload_plan(stokes_batch b, int ty) {
         cudaMemcpy(b->d_wl + nw, wc.data(), wc.size() * sizeof(int), cudaMemcpyHostToDevice);
         cudaMemcpy(b->d_wl + 2 * nw, wr.data(), wr.size() * sizeof(int), cudaMemcpyHostToDevice);
     }
+    if ((e = upload_patches(b, insts)) != cudaSuccess) return e;
     return cudaMemcpy(b->d_inst, insts.data(), insts.size() * sizeof(BInst), cudaMemcpyHostToDevice);
 }
 
@@ -374,7 +604,10 @@ static cudaError_t launch_persistent(stokes_batch b, int ty, int grid, int max_i
     const int* wi = b->d_wl;
     const int* wc = b->d_wl + nw;
     const int* wr = b->d_wl + 2 * nw;
+    const int* pli = b->d_pl;
+    const int* plp = b->d_pl ? b->d_pl + b->pl_cap : nullptr;
     void* args[] = {(void*)&b->d_inst, (void*)&b->d_st, (void*)&wi, (void*)&wc, (void*)&wr, (void*)&b->nwork,
+                    (void*)&pli, (void*)&plp, (void*)&b->npatch,
                     (void*)&b->d_part, (void*)&b->d_g, (void*)&b->n, (void*)&max_iter, (void*)&tol};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -386,7 +619,7 @@ static cudaError_t launch_persistent(stokes_batch b, int ty, int grid, int max_i
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, kernel_for(ty), args);
+    return cudaLaunchKernelExC(&cfg, kernel_for(ty, b->sw), args);
 }
 
 static std::string cache_path(const char* given) {
@@ -440,14 +673,15 @@ static std::string tune_key(stokes_batch b) {
     cudaGetDeviceProperties(&p, dev);
     std::string gpu = p.name;
     for (auto& ch : gpu) if (ch == ' ') ch = '_';
-    return "batch2d_fp64_n" + std::to_string(b->n) + "_slots2^" + std::to_string(lg) + "_" + gpu;
+    return std::string(b->sw ? "batch2d_fp64_schwarz_n" : "batch2d_fp64_n") + std::to_string(b->n) + "_slots2^" +
+           std::to_string(lg) + "_" + gpu;
 }
 
 static cudaError_t autotune(stokes_batch b, const char* cache) {
     std::string path = cache_path(cache), key = tune_key(b);
     int ty, cps;
     double us;
-    if (cache_lookup(path, key, ty, cps, us) && cps <= max_ctas_per_sm(ty)) {
+    if (cache_lookup(path, key, ty, cps, us) && cps <= max_ctas_per_sm(ty, b->sw)) {
         b->ty = ty; b->cps = cps; b->tuned_us = us;
         return upload_plan(b, ty);
     }
@@ -458,7 +692,7 @@ static cudaError_t autotune(stokes_batch b, const char* cache) {
     for (int t : {4, 8, 16}) {
         cudaError_t e = upload_plan(b, t);
         if (e != cudaSuccess) return e;
-        int mx = max_ctas_per_sm(t);
+        int mx = max_ctas_per_sm(t, b->sw);
         for (int c = 1; c <= std::min(mx, 4); ++c) {
             int grid = std::min(sms * c, std::max(1, b->nwork));
             // warm run, then a timed run of a fixed number of iterations
@@ -540,6 +774,7 @@ stokes_status stokes_batch_destroy(stokes_batch b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     cudaFree(b->d_inst); cudaFree(b->d_st); cudaFree(b->d_g); cudaFree(b->d_wl); cudaFree(b->d_part);
     cudaFree(b->d_st0); cudaFree(b->d_g0);
+    if (b->d_pl) cudaFree(b->d_pl);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     if (b->s) cudaStreamDestroy(b->s);
@@ -554,6 +789,7 @@ stokes_status stokes_batch_create(stokes_batch* out, int n, const stokes_ctx* ct
     auto* b = new stokes_batch_s();
     b->n = n;
     b->opt = *opt;
+    b->sw = opt->precond == 2;
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i] || ctxs[i]->c.L.dim != 2 || !ctxs[i]->c.have_weights) {
             delete b;
@@ -618,6 +854,17 @@ stokes_status stokes_batch_solve(stokes_batch b, const stokes_batch_io* io, stok
         cudaStreamSynchronize(b->c[i]->stream);
     }
     cudaError_t e = cudaSuccess;
+    if (b->sw) {
+        // the contexts' Schwarz plans are rebuilt after every weight build:
+        // refresh the instance table and patch list when any plan moved
+        bool moved = false;
+        for (int i = 0; i < b->n; ++i) {
+            const SchwarzPlan* P = nullptr;
+            if ((e = schwarz_ensure(b->c[i], &P)) != cudaSuccess) return STOKES_ERR_CUDA;
+            moved |= (int)b->plan_key.size() != b->n || P->inv != b->plan_key[i];
+        }
+        if (moved && (e = upload_plan(b, b->ty)) != cudaSuccess) return STOKES_ERR_CUDA;
+    }
     auto key = io_pointers(io, b->n);
     if (b->use_graph && (!b->graph || key != b->io_key)) {
         e = capture(b, io);

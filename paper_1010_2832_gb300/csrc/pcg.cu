@@ -290,8 +290,7 @@ static cudaError_t schwarz_build(Ctx* c) {
     if ((e = al((void**)&P.lmap, sizeof(short) * np * PMAX)) != cudaSuccess) return e;
     // FP32 factors: BF16 storage halves the local-solve traffic but, measured
     // on the 1024^2 bump workload, needs 4.4x the CG iterations
-    P.xbf16 = 0;
-    if ((e = al((void**)&P.inv, (P.xbf16 ? 2 : 4) * np * PFAC)) != cudaSuccess) return e;
+    if ((e = al((void**)&P.inv, sizeof(float) * np * PFAC)) != cudaSuccess) return e;
     if ((e = al((void**)&P.scale, sizeof(float) * np * PMAX)) != cudaSuccess) return e;
     if ((e = al((void**)&P.ybuf, sizeof(float) * ng * PMAX)) != cudaSuccess) return e;
     cudaMemcpyAsync(P.pid, pid.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, c->stream);
@@ -299,9 +298,7 @@ static cudaError_t schwarz_build(Ctx* c) {
     cudaMemsetAsync(P.ybuf, 0, sizeof(float) * ng * PMAX, c->stream);
     const int smem = SW_SETUP_SMEM;
     cudaFuncSetAttribute(k_schwarz_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_schwarz_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sw_gemv_smem<float>());
-    cudaFuncSetAttribute(k_schwarz_gemv<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         sw_gemv_smem<__nv_bfloat16>());
+    cudaFuncSetAttribute(k_schwarz_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize, SW_GEMV_SMEM);
     cudaEvent_t a, b;
     cudaEventCreate(&a); cudaEventCreate(&b);
     cudaEventRecord(a, c->stream);
@@ -727,6 +724,14 @@ cudaError_t apply_preconditioner(Ctx* c, int which, const float* r, float* z) {
 }
 
 double schwarz_setup_ms(Ctx* c) { return c->sw_ready ? c->sw_setup_ms : -1.0; }
+
+// The context's Schwarz plan for its current weights, built if needed.
+cudaError_t schwarz_ensure(Ctx* c, const SchwarzPlan** plan) {
+    cudaError_t e = cudaSuccess;
+    if (!c->sw_ready) e = schwarz_build(c);
+    if (plan) *plan = c->sw;
+    return e;
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free additive Schwarz apply.  For callers that cannot allocate

@@ -23,48 +23,17 @@
 //      the factor (X = L^-1) and store it in FP32 (BF16 loses the small-
 //      eigenvalue directions of the worst-conditioned patches, and those
 //      then cost many CG iterations on large grids).
-// Apply (every CG step): one warp per patch computes
-// z_p = D^-1/2 X^T X D^-1/2 r_p (FP32 accumulation), symmetric positive
+// Apply (every CG step): one CTA per patch computes
+// z_p = Q D^-1/2 X^T X D^-1/2 Q r_p (FP32 accumulation), symmetric positive
 // definite whatever the rounding of X; a gather kernel sums, for every
 // unknown, the contributions of the (at most four) patches covering it in a
-// fixed order, so the preconditioner is symmetric and deterministic.  Inactive unknowns get z = r.
+// fixed order, so the preconditioner is symmetric and deterministic.
+// Inactive unknowns get z = r.
 #include <cmath>
 #include <vector>
-#include "internal.cuh"
-#include "ctx.cuh"
+#include "schwarz_plan.cuh"
 
 namespace stk {
-
-constexpr int PB = 4;               // patch core (slots per side)
-constexpr int PR = PB + 2;          // with the one-slot ring
-constexpr int PMAX = 3 * PR * PR;   // unknowns per patch at most (2D: 108)
-// Packed lower triangle with every row padded to a multiple of 4 entries, so
-// rows start on 16-byte boundaries: row r (group m = r / 4, rows of group m
-// hold 4(m+1) entries) starts at 8 m (m+1) + (r - 4m) 4 (m+1).
-__host__ __device__ constexpr int tri4_off(int r) { return 8 * (r / 4) * (r / 4 + 1) + (r - 4 * (r / 4)) * 4 * (r / 4 + 1); }
-constexpr int PFAC = tri4_off(PMAX);                          // 6048 floats per patch
-
-struct SchwarzPlan {
-    int npx, npy;                   // patch grid over slots [0, nx] x [0, ny]
-    int* pid;                       // [npy * npx] compact patch id or -1
-    int* corner;                    // [np] packed (I, J)
-    int* nloc;                      // [np] active unknowns per patch
-    short* lmap;                    // [np * PMAX] local index of (f, jj, ii) or -1
-    void* inv;                      // [np * PFAC] X = L^-1 of each scaled patch matrix, padded packed
-                                    // rows, FP32 or (xbf16) BF16
-    int xbf16;
-    float* scale;                   // [np * PMAX] D^-1/2 of each patch, by position (f, jj, ii)
-    float* ybuf;                    // [npy * npx * PMAX] local results by grid patch and position
-                                    // (f, jj, ii); zero for inactive patches and positions
-    int np;
-};
-
-// slot (i, j) of a patch position; f = field (0 txx cell, 1 txy node, 2 p cell)
-__device__ __forceinline__ bool unknown_active(const DevArrays& D, const Layout& L, int f, int i, int j) {
-    if (i < 0 || j < 0 || i > L.nx || j > L.ny) return false;
-    if (f != 1 && (i >= L.nx || j >= L.ny)) return false;
-    return D.act[f == 1 ? 1 : 0][L.off(i + 1, j + 1, 0)] != 0;
-}
 
 __global__ void k_schwarz_mark(Layout L, DevArrays D, int npx, int npy, int* flag) {
     int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y;
@@ -288,64 +257,19 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
     for (int e = t; e < n * n4; e += 256) {
         int r = e / n4, c = e % n4;
         if (c < (r / 4 + 1) * 4) {
-            const float v = c <= r ? X[r * PMAX + c] : 0.f;
-            const int64_t at = (int64_t)p * PFAC + tri4_off(r) + c;
-            if (P.xbf16) static_cast<__nv_bfloat16*>(P.inv)[at] = __float2bfloat16(v);
-            else static_cast<float*>(P.inv)[at] = v;
+            P.inv[(int64_t)p * PFAC + tri4_off(r) + c] = c <= r ? X[r * PMAX + c] : 0.f;
         }
     }
     for (int e = t; e < PMAX; e += 256) P.scale[(int64_t)p * PMAX + e] = map[e] >= 0 ? sc[map[e]] : 0.f;
 }
 
-// Shared-memory address of a pointer (for mbarrier and bulk-copy operands).
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Polls of the bulk copy's mbarrier before a local solve gives up (each
-// try_wait itself blocks for a while); the copy of 23 KB takes microseconds.
-constexpr long long SW_WAIT_POLLS = 1LL << 22;
-
-// Wait for phase `parity` of an mbarrier, at most SW_WAIT_POLLS polls.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (long long i = 0; i < SW_WAIT_POLLS; ++i) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
 // Bytes of patch p's packed factor (a multiple of 16).
-template <class T>
 __device__ __forceinline__ uint32_t sw_bytes(const SchwarzPlan& P, int p) {
-    return (uint32_t)((tri4_off(P.nloc[p]) * (int)sizeof(T) + 15) / 16 * 16);
+    return (uint32_t)(tri4_off(P.nloc[p]) * (int)sizeof(float));      // a multiple of 16
 }
 
-// four consecutive stored entries as floats (16-byte or 8-byte loads)
+// four consecutive stored entries (one 16-byte load)
 __device__ __forceinline__ float4 ld4(const float* x) { return *reinterpret_cast<const float4*>(x); }
-__device__ __forceinline__ float4 ld4(const __nv_bfloat16* x) {
-    const uint2 u = *reinterpret_cast<const uint2*>(x);
-    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
-    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
-    return make_float4(a.x, a.y, b.x, b.y);
-}
-
-// Start the bulk (TMA) copy of one packed factor into shared memory,
-// completing on mbarrier `bar` (one thread).
-__device__ __forceinline__ void sw_issue(uint32_t bar, void* dst, const void* src, uint32_t bytes) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    if (bytes > 0)
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                         smem_u32(dst)),
-                     "l"(src), "r"(bytes), "r"(bar)
-                     : "memory");
-}
 
 // z_p = Q D^-1/2 X^T X D^-1/2 Q r_p with X = L^-1, one CTA (128 threads)
 // per active patch.  Thread 0 starts a bulk (TMA) copy of the packed factor
@@ -357,11 +281,9 @@ __device__ __forceinline__ void sw_issue(uint32_t bar, void* dst, const void* sr
 // eight CTAs share an SM and their copies overlap each other's arithmetic.
 // A copy that never completes (bounded wait) marks the solve
 // STOKES_ERR_TIMEOUT and ends it.
-template <class T>
 __global__ void __launch_bounds__(128) k_schwarz_gemv(Layout L, SchwarzPlan P, const float* __restrict__ r,
                                                       CgScalars* sc) {
-    extern __shared__ __align__(128) unsigned char xs_raw[];   // PFAC entries of T
-    T* Xs = reinterpret_cast<T*>(xs_raw);
+    extern __shared__ __align__(128) float Xs[];               // PFAC floats
     __shared__ __align__(16) float s[PMAX];
     __shared__ float y[PMAX];
     __shared__ __align__(8) unsigned long long bar;
@@ -373,7 +295,7 @@ __global__ void __launch_bounds__(128) k_schwarz_gemv(Layout L, SchwarzPlan P, c
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_addr), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        sw_issue(b_addr, Xs, static_cast<const T*>(P.inv) + (int64_t)p * PFAC, sw_bytes<T>(P, p));
+        sw_issue(b_addr, Xs, P.inv + (int64_t)p * PFAC, sw_bytes(P, p));
     }
     constexpr float H = 0.70710678118654752f;
     const int n = P.nloc[p];
@@ -423,9 +345,9 @@ __global__ void __launch_bounds__(128) k_schwarz_gemv(Layout L, SchwarzPlan P, c
         }
         return;
     }
-    const T* X = Xs;
+    const float* X = Xs;
     if (t < n) {
-        const T* xr = X + tri4_off(t);
+        const float* xr = X + tri4_off(t);
         const float4* s4 = reinterpret_cast<const float4*>(s);
         float acc = 0.f;
         for (int j = 0; j <= t / 4; ++j) {
@@ -480,14 +402,12 @@ __global__ void __launch_bounds__(128) k_schwarz_gemv(Layout L, SchwarzPlan P, c
     }
 }
 
-// dynamic shared memory of k_schwarz_gemv<T>: the packed factor
-template <class T> constexpr int sw_gemv_smem() { return PFAC * (int)sizeof(T); }
+// dynamic shared memory of k_schwarz_gemv: the packed factor
+constexpr int SW_GEMV_SMEM = PFAC * (int)sizeof(float);
 
 static inline void launch_schwarz_gemv(const Layout& L, const SchwarzPlan& P, const float* r, CgScalars* sc,
                                        cudaStream_t s) {
-    if (!P.np) return;
-    if (P.xbf16) k_schwarz_gemv<__nv_bfloat16><<<P.np, 128, sw_gemv_smem<__nv_bfloat16>(), s>>>(L, P, r, sc);
-    else k_schwarz_gemv<float><<<P.np, 128, sw_gemv_smem<float>(), s>>>(L, P, r, sc);
+    if (P.np) k_schwarz_gemv<<<P.np, 128, SW_GEMV_SMEM, s>>>(L, P, r, sc);
 }
 
 __device__ __forceinline__ void schwarz_gather_slot(const Layout& L, const DevArrays& D, const SchwarzPlan& P,
