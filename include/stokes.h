@@ -193,6 +193,24 @@ typedef struct {
 void stokes_default_options(stokes_options* o);
 
 /*
+ * Prescribed surface pressure p_BC and deviatoric stress tau_BC (Section 6.1,
+ * a traction boundary such as surface tension): writes to u_star_out[d] the
+ * u* to pass to stokes_solve_step.  The section's force enters the first
+ * block row of eq. stokesmixedsystem weighted like the mass term, so on live
+ * faces u*_out = u* + dt/(rho W_L^u) f with
+ *   f = W_A^u (M^T x_BC) - M^T (W_A x_BC),  M^T = [D^T | G],
+ * W_A = 1 - W_L the air fraction of each sample (1 for eliminated unknowns),
+ * x_BC = (tau_BC, p_BC); elsewhere u*_out = u*.  The sign is the opposite of
+ * the one printed: with it a uniform p_BC = P0 on liquid at rest gives the
+ * liquid pressure P0 (the printed sign gives -P0).  tau_bc[s] (stress kinds
+ * in slot-field order) and p_bc use the layout of stokes_solve_step's
+ * tau_out and p_out; all device arrays; u_star_out may be u_star.  Uses the
+ * solver's work vectors (do not overlap with a solve on this context).
+ */
+stokes_status stokes_traction_u_star(stokes_ctx ctx, const double* const* tau_bc, const double* p_bc,
+                                     const double* const* u_star, double* const* u_star_out);
+
+/*
  * One implicit step (the hot path): b from u*, solve A x = b to the
  * requested true relative residual, recover u.  Inputs u_star[d] and outputs
  * u_out[d], tau_out[s] (stress kinds in slot-field order without p) and

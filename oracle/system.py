@@ -231,21 +231,55 @@ def rhs(S: StokesSystem, u_star=None) -> np.ndarray:
     return S.a * (S.M @ v) - S.a * WSx * (S.M @ S.u_bc)
 
 
-def recover_velocity(S: StokesSystem, x: np.ndarray):
+def traction_force(S: StokesSystem, x_bc: np.ndarray) -> np.ndarray:
+    """Face force of prescribed surface pressure and deviatoric stress
+    (Section 6.1), x_bc = (tau_BC, p_BC) in unknown order, at every sample:
+
+        f = W_A^u (M^T x_BC) - M^T (W_A^x x_BC),   W_A = 1 - W_L (air fraction),
+
+    with M^T = [D^T | G].  The section prints the opposite sign; with it a
+    uniform surface pressure P0 on liquid at rest gives liquid pressure -P0.
+    The boundary integral it starts from carries the traction's work with the
+    liquid's outward normal while its integration by parts uses the air's, so
+    the sign is taken that gives +P0 (tested).  The air fraction of an
+    unknown's sample is 1 - W_L if the unknown is active and 1 if it was
+    eliminated (Section 8): an eliminated unknown carries no liquid, and
+    with this reading the uniform-pressure state is exact."""
+    WAx = 1.0 - S.WLx * S.active
+    WAu = 1.0 - S.WLu
+    return WAu * (S.M.T @ x_bc) - S.M.T @ (WAx * x_bc)
+
+
+def traction_u_star(S: StokesSystem, x_bc: np.ndarray, u_star=None) -> np.ndarray:
+    """u* carrying the prescribed-traction terms: the force f enters the first
+    block row of eq. stokesmixedsystem weighted like the mass term (by W_F^u,
+    the same reading as for the prescribed-velocity terms), so eliminating the
+    velocity gives u* + dt f / (rho W_L^u) on live faces and u* elsewhere.
+    Solve with rhs(S, result) and recover with it."""
+    us = S.u_star if u_star is None else u_star
+    f = traction_force(S, x_bc)
+    out = np.array(us, dtype=np.float64, copy=True)
+    lv = S.live
+    out[lv] = us[lv] + S.inp.dt / (S.rho[lv] * S.WLu[lv]) * f[lv]
+    return out
+
+
+def recover_velocity(S: StokesSystem, x: np.ndarray, u_star=None):
     """Face velocities from (tau, p); first block row of eq. stokesmixedsystem.
 
     Live faces: u* - dt/(rho W_L^u) (B^T x).  Faces with effective W_F^u = 0
     (solid, wall, invalid): u_BC.  Bad faces (fluid but no liquid): u*.
     """
+    us = S.u_star if u_star is None else u_star
     Btx = S.B.T @ x
-    u = np.where(S.effWF == 0, S.u_bc, S.u_star)
+    u = np.where(S.effWF == 0, S.u_bc, us)
     lv = S.live
     u = u.copy()
-    u[lv] = S.u_star[lv] - S.inp.dt / (S.rho[lv] * S.WLu[lv]) * Btx[lv]
+    u[lv] = us[lv] - S.inp.dt / (S.rho[lv] * S.WLu[lv]) * Btx[lv]
     return u
 
 
-def kkt_system(S: StokesSystem):
+def kkt_system(S: StokesSystem, face_force=None):
     """Indefinite KKT of eq. stokesmixedsystem on (live faces, active unknowns).
 
     Returns (matrix, rhs, live_index, active_index).  Row 1 keeps the paper's
@@ -264,7 +298,10 @@ def kkt_system(S: StokesSystem):
     WSu = 1.0 - S.effWF
     WSx = 1.0 - S.WFx
     g = -S.a * (S.M @ (WSu * S.u_bc)) + S.a * WSx * (S.M @ S.u_bc)
-    r = np.concatenate([mass * S.u_star[lv], g[ac]])
+    top_rhs = mass * S.u_star[lv]
+    if face_force is not None:           # prescribed traction, weighted like the mass term
+        top_rhs = top_rhs + (S.effWF * face_force)[lv]
+    r = np.concatenate([top_rhs, g[ac]])
     return Kmat, r, lv, ac
 
 

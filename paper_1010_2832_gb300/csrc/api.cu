@@ -13,6 +13,7 @@ using namespace stk;
 namespace stk {
 void set_error(Ctx* c, const std::string& m) { c->err = m; }
 cudaError_t launch_unpack(Ctx* c, const double* slots, double* const* fields, int to_fields);
+cudaError_t launch_traction(Ctx* c, const double* const* bc_fields, const double* const* ustar, double* const* uout);
 void apply_set_attributes();
 cudaError_t bench_cg_kernels(Ctx* c, int precision, int launches, double* ms_apply, double* ms_update);
 cudaError_t bench_schwarz_kernels(Ctx* c, int launches, double* ms_local, double* ms_gather, double* bytes_local);
@@ -365,6 +366,24 @@ stokes_status stokes_solve_system(stokes_ctx h, const double* b, double* x, cons
         st->ms_rhs = st->ms_recover = 0.0;
     }
     return s;
+}
+
+stokes_status stokes_traction_u_star(stokes_ctx h, const double* const* tau_bc, const double* p_bc,
+                                     const double* const* u_star, double* const* u_star_out) {
+    if (!h) return STOKES_ERR_ARG;
+    Ctx& c = h->c;
+    if (!tau_bc || !p_bc || !u_star || !u_star_out) { c.err = "null argument"; return STOKES_ERR_ARG; }
+    for (int d = 0; d < c.nd; ++d)
+        if (!u_star[d] || !u_star_out[d]) { c.err = "null face component"; return STOKES_ERR_ARG; }
+    const double* fields[6];
+    for (int f = 0; f < c.nf - 1; ++f) {
+        if (!tau_bc[f]) { c.err = "null stress component"; return STOKES_ERR_ARG; }
+        fields[f] = tau_bc[f];
+    }
+    fields[c.nf - 1] = p_bc;
+    if (!c.have_weights) { c.err = "stokes_build_weights has not run"; return STOKES_ERR_STATE; }
+    API_CHECK_CUDA(h, launch_traction(&c, fields, u_star, u_star_out));
+    return STOKES_OK;
 }
 
 stokes_status stokes_solve_step(stokes_ctx h, const double* const* u_star, double* const* u_out,

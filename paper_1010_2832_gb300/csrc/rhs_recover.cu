@@ -270,4 +270,120 @@ cudaError_t launch_unpack(Ctx* c, const double* slots, double* const* fields, in
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Prescribed traction (Section 6.1): the face force
+//   f = W_A^u (M^T x_BC) - M^T (W_A^x x_BC),  W_A = 1 - W_L (1 on eliminated
+//   unknowns), M^T = [D^T | G],
+// enters the first block row weighted like the mass term, so it shifts u* on
+// live faces by dt/(rho W_L^u) f (the recovery coefficient).  The section
+// prints the force with the opposite sign, which would give a liquid under a
+// uniform surface pressure P0 the pressure -P0; this sign gives +P0.
+// ---------------------------------------------------------------------------
+
+// xa = W_A * xb per unknown field, on every slot (xb is zero where no sample
+// exists)
+__global__ void k_air_weight(Layout L, DevArrays D, int nf, const double* xb, double* xa) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    int k = blockIdx.z;
+    if (i > L.nx || j > L.ny || (L.dim == 3 && k > L.nz)) return;
+    const int64_t o = L.off(i + 1, j + 1, L.dim == 2 ? 0 : k + 1);
+    for (int f = 0; f < nf; ++f) {
+        // W_L kind and activity site of unknown field f
+        int kind, site;
+        if (L.dim == 2) { kind = f == 1 ? 1 : 0; site = f == 1 ? 1 : 0; }
+        else if (f <= 1 || f == 5) { kind = 0; site = 0; }
+        else { kind = f + 2; site = f - 1; }
+        const double wl = D.act[site][o] ? D.WL[kind][o] : 0.0;
+        xa[(int64_t)f * L.stride + o] = (1.0 - wl) * xb[(int64_t)f * L.stride + o];
+    }
+}
+
+__global__ void k_traction2d(Layout L, DevArrays D, const double* xa, const double* xb, FacePtrs us, FaceOut out,
+                             double inv_h) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > L.nx || j > L.ny) return;
+    const int64_t S = L.stride;
+    int c = i + 1, r = j + 1;
+    int64_t o = L.off(c, r, 0);
+    for (int d = 0; d < 2; ++d) {
+        if (d == 0 && j >= L.ny) continue;
+        if (d == 1 && i >= L.nx) continue;
+        const int64_t fi = fidx2(2 + d, i, j, L.nx, L.ny);
+        double u = us.p[d][fi];
+        if (D.fflag[d][o] & F_LIVE) {
+            // (M^T v) on this face for v = xa and v = xb
+            auto mt = [&](const double* x) {
+                auto U = [&](int64_t oo) { return x[2 * S + oo] - x[oo]; };
+                auto V = [&](int64_t oo) { return x[2 * S + oo] + x[oo]; };
+                auto N = [&](int64_t oo) { return x[S + oo]; };
+                return d == 0 ? (U(o) - U(L.off(c - 1, r, 0))) + (N(o) - N(L.off(c, r + 1, 0)))
+                              : (V(o) - V(L.off(c, r - 1, 0))) + (N(o) - N(L.off(c + 1, r, 0)));
+            };
+            const double wa = 1.0 - D.WL[2 + d][o];
+            const double f = inv_h * (wa * mt(xb) - mt(xa));
+            u += D.rec[d][o] * f;
+        }
+        out.p[d][fi] = u;
+    }
+}
+
+__global__ void k_traction3d(Layout L, DevArrays D, const double* xa, const double* xb, FacePtrs us, FaceOut out,
+                             double inv_h) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    int k = blockIdx.z;
+    if (i > L.nx || j > L.ny || k > L.nz) return;
+    const int64_t S = L.stride;
+    int c = i + 1, r = j + 1, q = k + 1;
+    int64_t o = L.off(c, r, q);
+    for (int d = 0; d < 3; ++d) {
+        bool ex = d == 0 ? (j < L.ny && k < L.nz) : d == 1 ? (i < L.nx && k < L.nz) : (i < L.nx && j < L.ny);
+        if (!ex) continue;
+        const int64_t fi = fidx3(1 + d, i, j, k, L.nx, L.ny, L.nz);
+        double u = us.p[d][fi];
+        if (D.fflag[d][o] & F_LIVE) {
+            auto mt = [&](const double* x) {
+                auto Uc = [&](int64_t oo) { return x[5 * S + oo] - x[oo]; };
+                auto Vc = [&](int64_t oo) { return x[5 * S + oo] - x[S + oo]; };
+                auto Wc = [&](int64_t oo) { return x[5 * S + oo] + x[oo] + x[S + oo]; };
+                auto Nxy = [&](int64_t oo) { return x[2 * S + oo]; };
+                auto Nxz = [&](int64_t oo) { return x[3 * S + oo]; };
+                auto Nyz = [&](int64_t oo) { return x[4 * S + oo]; };
+                if (d == 0)
+                    return (Uc(o) - Uc(L.off(c - 1, r, q))) + (Nxy(o) - Nxy(L.off(c, r + 1, q))) +
+                           (Nxz(o) - Nxz(L.off(c, r, q + 1)));
+                if (d == 1)
+                    return (Vc(o) - Vc(L.off(c, r - 1, q))) + (Nxy(o) - Nxy(L.off(c + 1, r, q))) +
+                           (Nyz(o) - Nyz(L.off(c, r, q + 1)));
+                return (Wc(o) - Wc(L.off(c, r, q - 1))) + (Nxz(o) - Nxz(L.off(c + 1, r, q))) +
+                       (Nyz(o) - Nyz(L.off(c, r + 1, q)));
+            };
+            const double wa = 1.0 - D.WL[1 + d][o];
+            const double f = inv_h * (wa * mt(xb) - mt(xa));
+            u += D.rec[d][o] * f;
+        }
+        out.p[d][fi] = u;
+    }
+}
+
+// u*_out = u* + dt/(rho W_L^u) f on live faces, u* elsewhere.  The prescribed
+// fields (tau_BC fields then p_BC, field layout) go through two of the
+// solver's work vectors.
+cudaError_t launch_traction(Ctx* c, const double* const* bc_fields, const double* const* ustar, double* const* uout) {
+    const Layout& L = c->L;
+    double* xb = c->w64.z;
+    double* xa = c->w64.q;
+    cudaError_t e = launch_unpack(c, xb, (double* const*)bc_fields, 0);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(xa, 0, sizeof(double) * c->vec_elems(), c->stream)) != cudaSuccess) return e;
+    k_air_weight<<<slot_grid(L), dim3(32, 8), 0, c->stream>>>(L, c->A, c->nf, xb, xa);
+    FacePtrs us{{ustar[0], ustar[1], L.dim == 3 ? ustar[2] : nullptr}};
+    FaceOut out{{uout[0], uout[1], L.dim == 3 ? uout[2] : nullptr}};
+    if (L.dim == 2) k_traction2d<<<slot_grid(L), dim3(32, 8), 0, c->stream>>>(L, c->A, xa, xb, us, out, 1.0 / c->g.h);
+    else k_traction3d<<<slot_grid(L), dim3(32, 8), 0, c->stream>>>(L, c->A, xa, xb, us, out, 1.0 / c->g.h);
+    return cudaGetLastError();
+}
+
 }  // namespace stk

@@ -53,7 +53,7 @@ EXPORTED = ("stokes_create", "stokes_destroy", "stokes_last_error", "stokes_buil
             "stokes_net_gradient", "stokes_net_train_step", "stokes_set_learned_preconditioner",
             "stokes_learned_grid", "stokes_learned_features", "stokes_learned_targets",
             "stokes_learned_jacobi_steps", "stokes_apply_preconditioner", "stokes_schwarz_setup_ms",
-            "stokes_apply_schwarz_noalloc", "stokes_bench_schwarz_kernels")
+            "stokes_apply_schwarz_noalloc", "stokes_bench_schwarz_kernels", "stokes_traction_u_star")
 
 
 class BatchIO(C.Structure):
@@ -115,6 +115,7 @@ def load_library(path=LIB_PATH):
         "stokes_schwarz_setup_ms": (D, [P]),
         "stokes_apply_schwarz_noalloc": (I, [P, P, P]),
         "stokes_bench_schwarz_kernels": (I, [P, I, C.POINTER(D), C.POINTER(D), C.POINTER(D)]),
+        "stokes_traction_u_star": (I, [P, PP, P, PP, PP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -228,6 +229,14 @@ class StokesContext:
         if rc not in (0, -3):
             self._check(rc)
         return st
+
+    def traction_u_star(self, tau_bc, p_bc, u_star, u_star_out):
+        """u* carrying a prescribed surface pressure / deviatoric stress
+        (stokes_traction_u_star); lists of FP64 device tensors."""
+        tp, ta = _ptrs([_dev(t) for t in tau_bc])
+        up, ua = _ptrs([_dev(t) for t in u_star])
+        op, oa = _ptrs([_dev(t) for t in u_star_out])
+        self._check(self.lib.stokes_traction_u_star(self.h, tp, _dev(p_bc).data_ptr(), up, op))
 
     def solve_step(self, u_star, u_out, tau_out, p_out, options=None):
         o = options or default_options()

@@ -248,3 +248,81 @@ def test_additive_schwarz_is_symmetric_positive():
     Ma, Mb = So.additive_schwarz(S, a), So.additive_schwarz(S, b)
     assert abs(Ma @ b - a @ Mb) <= 1e-10 * np.linalg.norm(Ma) * np.linalg.norm(b)
     assert a @ Ma > 0
+
+
+def _x_bc(S, tau=None, p=None):
+    """(tau_BC, p_BC) in unknown order from per-sample callables or zeros."""
+    parts = []
+    nx, ny, nz = S_._nx_ny_nz(S.inp.n)
+    names = S_.unknown_names(S.inp.dim)
+    kinds = S_.unknown_kinds(S.inp.dim)
+    for name, kind in zip(names, kinds):
+        size = S.sizes[kind]
+        fn = p if name == "p" else (tau or {}).get(name)
+        if fn is None:
+            parts.append(np.zeros(size))
+        else:
+            P = W.sample_points(kind, S.inp.n, S.inp.h, S.inp.origin)
+            parts.append(np.ravel(fn(P) * np.ones(P[0].shape)))
+    return np.concatenate(parts)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_uniform_surface_pressure_is_hydrostatic(dim):
+    """A uniform prescribed pressure P0 on a free surface, liquid at rest and no
+    body force: the liquid pressure is P0, the stresses and velocities zero
+    (Section 6.1's traction terms, with the sign that makes this hold)."""
+    if dim == 2:
+        wl = W.disk_in_box(24, radius=0.3)
+    else:
+        lo, hi = (0.0,) * 3, (1.0,) * 3
+        wl = W.from_functions("ball", 3, (10, 10, 10), 0.1, 0.01, lo,
+                              lambda X: np.sqrt(sum((x - 0.5) ** 2 for x in X)) - 0.3, lambda X: W.box_phi(X, lo, hi),
+                              lambda P: 1.0, lambda P: 1.0, lambda d, P: 0.0, lambda d, P: 0.0)
+    S = _system(wl)
+    P0 = 2.5
+    xbc = _x_bc(S, p=lambda P: P0)
+    zero = np.zeros_like(S.u_star)
+    ue = S_.traction_u_star(S, xbc, u_star=zero)
+    b = S_.rhs(S, ue) if np.all(S.u_bc == 0) else None
+    if b is None:
+        pytest.skip("moving boundary in this geometry")
+    x = So.solve_direct(S.A, b, S_.pressure_null_vectors(S))
+    parts = S_.split_unknowns(S, x)
+    act = S_.split_unknowns(S, S.active.astype(float))
+    pa = parts["p"][act["p"] > 0]
+    assert pa.size > 0
+    assert np.abs(pa - P0).max() <= 1e-9 * P0
+    for name in parts:
+        if name != "p":
+            assert np.abs(parts[name]).max() <= 1e-9 * P0
+    u = S_.recover_velocity(S, x, u_star=ue)
+    assert np.abs(u[S.live]).max() <= 1e-9 * P0 * S.inp.dt / S.inp.h
+
+
+def test_traction_terms_match_the_kkt_system():
+    """The SPD route with u* + dt f/(rho W_L) equals the KKT solve with the
+    force added to the first block row (weighted like the mass term), and
+    the force is linear in (tau_BC, p_BC)."""
+    wl = W.bumps_2d(20, seed=9, rho_split=False)
+    S = _system(wl)
+    rng = np.random.default_rng(3)
+    xbc = rng.normal(size=S.A.shape[0])
+    f = S_.traction_force(S, xbc)
+    ue = S_.traction_u_star(S, xbc)
+    x = So.solve_direct(S.A, S_.rhs(S, ue), S_.pressure_null_vectors(S))
+    u = S_.recover_velocity(S, x, u_star=ue)
+    Kmat, r, lv, ac = S_.kkt_system(S, face_force=f)
+    z = spla.spsolve(Kmat.tocsc(), r)
+    scale = max(np.abs(z[:lv.size]).max(), 1e-30)
+    assert np.abs(u[lv] - z[:lv.size]).max() <= 1e-7 * scale
+    x2 = rng.normal(size=xbc.size)
+    f2 = S_.traction_force(S, x2)
+    assert np.allclose(S_.traction_force(S, 2 * xbc - 3 * x2), 2 * f - 3 * f2, atol=1e-12 * np.abs(f).max())
+    # no force far from the air: on a live face whose neighbouring unknowns
+    # are all active with W_L = 1 (and W_L^u = 1) both terms cancel
+    far = (S.WLu == 1.0) & S.live
+    nb_full = np.abs(S.M.T) @ ((S.WLx * S.active) < 1.0).astype(float) == 0
+    sel = far & nb_full
+    assert sel.any()
+    assert np.abs(f[sel]).max() <= 1e-12 * np.abs(f).max()
