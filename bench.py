@@ -135,7 +135,7 @@ def run_batched(args, rank, world):
     from paper_1010_2832_gb300 import stokes, workloads as W
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    wls = W.batch_instances(count=64, seed0=4000 + 1000 * rank)
+    wls = W.batch_instances(count=64, seed0=replica_seed(4000, 1000 * rank))
     made = [stokes.context_for(wl) for wl in wls]
     ctxs = [m[0] for m in made]
     devs = [m[1] for m in made]
@@ -156,6 +156,9 @@ def run_batched(args, rank, world):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(args.warmup):
         stats, ms = batch.solve(*args_io)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     times = []
     with ClockSampler(dev.index) as clk:
         for k in range(args.steps):
@@ -168,7 +171,9 @@ def run_batched(args, rank, world):
             ev1.record()
             torch.cuda.synchronize()
             times.append(ev0.elapsed_time(ev1))
-    ms_step = float(np.mean(times))
+    if world > 1:
+        torch.distributed.barrier()
+    ms_step = max_over_ranks(float(np.mean(times)), world, dev)
     # baseline: the same instances one at a time (plain FP64 Jacobi-PCG, graph loop)
     seq_ms, seq_iters = 0.0, []
     opt_plain = stokes.default_options(mode=0, tol=args.tol, precond=0)
@@ -195,10 +200,25 @@ def run_batched(args, rank, world):
     }
 
 
+def replica_seed(base, rank):
+    """Seed of rank ``rank``'s instance: every replica solves its own problem."""
+    return base + rank
+
+
+def max_over_ranks(value, world, device=None):
+    """Largest value over the ranks (the slowest replica sets the step time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_workload(name, rank):
     from paper_1010_2832_gb300 import workloads as W
     if name == "bumps1024":
-        return W.bumps_2d(1024, seed=2 + rank)
+        return W.bumps_2d(1024, seed=replica_seed(2, rank))
     if name == "column256":
         return W.column_3d(256)
     if name == "column128":
@@ -276,11 +296,7 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     if args.quick:   # profiling runs: the timed steps only
         return {"quick": True, "ms": times, "stats": stats}, wl
-    ms = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(times)), world, dev)
     bad = [s for s in stats if s["status"] != 0 or s["rel_residual"] > args.tol]
     iters = int(np.mean([s["iterations"] for s in stats]))
     outer = int(np.mean([s["outer"] for s in stats]))
