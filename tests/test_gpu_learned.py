@@ -82,3 +82,53 @@ def test_trained_network_vs_jacobi(tmp_path):
         with open(os.path.join(out_dir, "learned_vs_jacobi.json"), "w") as f:
             json.dump(dict(train_loss=losses, results=results), f)
     print("learned vs jacobi:", results)
+
+
+def test_trained_network_3d_vs_jacobi_and_plain_fp64():
+    """Config 5 at reduced scale (3D Gaussian-bump instances: training on 24^3,
+    evaluation on a held-out 32^3 instance): the trained network, the
+    untrained one, Jacobi alone (same mixed-precision solve) and plain FP64
+    Jacobi-PCG, on iterations and wall time.  These systems are stiff (tens
+    of thousands of Jacobi iterations).  The learned solve must converge like
+    the others; the comparison is recorded, not assumed."""
+    require_gpu()
+    from paper_1010_2832_gb300 import learned, stokes, workloads as W
+    from oracle import unet as U
+    train_wls = [W.bumps_3d(24, seed=5000 + i) for i in range(4)]
+    eval_wls = [W.bumps_3d(32, seed=9000)]
+    grids = []
+    for wl in train_wls[:1] + eval_wls[:1]:
+        ctx, dev = stokes.context_for(wl)
+        grids.append(stokes.learned_grid(ctx))
+    (Dt, Ht, Wt, cin, cout), (De, He, We, _, _) = grids
+    net = stokes.Net(3, cin, cout, max(4 * Dt * Ht * Wt, De * He * We))
+    net.set_params(net.from_oracle_layout(U.init_params(3, cin, cout, seed=3)))
+    net0 = stokes.Net(3, cin, cout, De * He * We)
+    net0.set_params(net.get_params())
+    data = []
+    for i, wl in enumerate(train_wls):
+        ctx, dev = stokes.context_for(wl)
+        stokes.attach_network(ctx, net)
+        xs, ys = learned.make_pairs(ctx, wl, 10, seed0=2000 * (i + 1))
+        data += list(zip(xs, ys))
+    losses = learned.train(net, data, (Dt, Ht, Wt), epochs=10, batch=4, lr=2e-3)
+    assert all(np.isfinite(losses))
+    results = []
+    for wl in eval_wls:
+        ctx, dev = stokes.context_for(wl)
+        row = {}
+        for name, mode, prec, use in (("learned", 1, 1, net), ("untrained", 1, 1, net0), ("jacobi_fp32", 1, 0, None),
+                                      ("plain_fp64", 0, 0, None)):
+            if use is not None:
+                stokes.attach_network(ctx, use)
+            st, ms, _ = learned.solve(ctx, dev, mode=mode, precond=prec, max_iter=400000)
+            row[name] = dict(status=st["status"], iterations=st["iterations"], ms=ms, rel=st["rel_residual"],
+                             jacobi_fallback_steps=stokes.learned_jacobi_steps(ctx) if prec == 1 else 0)
+            if name != "untrained":
+                assert st["status"] == 0 and st["rel_residual"] <= 1.01e-8, (name, st)
+        results.append(row)
+    out_dir = os.environ.get("STOKES_RESULTS_DIR")
+    if out_dir:
+        with open(os.path.join(out_dir, "learned_3d.json"), "w") as f:
+            json.dump(dict(train_loss=losses, results=results), f)
+    print("learned 3D:", results)
