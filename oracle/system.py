@@ -77,6 +77,7 @@ class StokesSystem:
     W_F: dict = field(default_factory=dict)
     # face-ordered vectors
     WLu: np.ndarray = None
+    WLm: np.ndarray = None
     WFu: np.ndarray = None
     effWF: np.ndarray = None
     invalid_face: np.ndarray = None
@@ -151,9 +152,17 @@ def _stress_block_C(dim, n, WLx, WFx, mux, active, sizes):
     return (sp.diags(d, format="csr") + Coff).tocsr()
 
 
-def build_system(inp: StokesInput, solid_side_rule: bool = True) -> StokesSystem:
+def build_system(inp: StokesInput, solid_side_rule: bool = True, min_face_liquid: float = 0.0) -> StokesSystem:
     """Assemble A and b.  ``solid_side_rule=False`` skips step 2 of the
-    null-space elimination (kept only to show in a test why it is needed)."""
+    null-space elimination (kept only to show in a test why it is needed).
+
+    ``min_face_liquid`` = eps > 0 floors the liquid fraction of live faces
+    where it is the face's mass (K, the velocity recovery, the traction
+    force): W_L^u -> max(W_L^u, eps).  The paper is silent on slivers; a
+    face whose control volume holds a rounding-level amount of liquid (a
+    level set that vanishes on lattice points) otherwise makes K, and the
+    condition number, arbitrarily large.  eps = 0 (the default) is the
+    paper's system unchanged."""
     S = StokesSystem(inp=inp)
     dim, n, h, dt = inp.dim, tuple(inp.n), inp.h, inp.dt
     sizes = sample_sizes(dim, n)
@@ -190,8 +199,9 @@ def build_system(inp: StokesInput, solid_side_rule: bool = True) -> StokesSystem
     # 3. live / bad faces
     S.live = (effWF > 0) & (S.WLu > 0)
     S.bad = (effWF > 0) & (S.WLu == 0)
+    S.WLm = np.where(S.live, np.maximum(S.WLu, min_face_liquid), S.WLu)   # face mass fraction
     S.K = np.zeros_like(effWF)
-    S.K[S.live] = dt * effWF[S.live] / (S.rho[S.live] * S.WLu[S.live])
+    S.K[S.live] = dt * effWF[S.live] / (S.rho[S.live] * S.WLm[S.live])
     # 4. free-surface side: unknowns coupled to a bad face
     touches_bad = (adj @ S.bad.astype(np.float64)) > 0
     cand = (S.WLx > 0) & ~touches_bad
@@ -260,7 +270,7 @@ def traction_u_star(S: StokesSystem, x_bc: np.ndarray, u_star=None) -> np.ndarra
     f = traction_force(S, x_bc)
     out = np.array(us, dtype=np.float64, copy=True)
     lv = S.live
-    out[lv] = us[lv] + S.inp.dt / (S.rho[lv] * S.WLu[lv]) * f[lv]
+    out[lv] = us[lv] + S.inp.dt / (S.rho[lv] * S.WLm[lv]) * f[lv]
     return out
 
 
@@ -275,7 +285,7 @@ def recover_velocity(S: StokesSystem, x: np.ndarray, u_star=None):
     u = np.where(S.effWF == 0, S.u_bc, us)
     lv = S.live
     u = u.copy()
-    u[lv] = us[lv] - S.inp.dt / (S.rho[lv] * S.WLu[lv]) * Btx[lv]
+    u[lv] = us[lv] - S.inp.dt / (S.rho[lv] * S.WLm[lv]) * Btx[lv]
     return u
 
 
@@ -289,7 +299,7 @@ def kkt_system(S: StokesSystem, face_force=None):
     dt = S.inp.dt
     lv = np.flatnonzero(S.live)
     ac = np.flatnonzero(S.active)
-    mass = (S.rho * S.effWF * S.WLu / dt)[lv]
+    mass = (S.rho * S.effWF * S.WLm / dt)[lv]
     Bw = (S.B @ sp.diags(S.effWF)).tocsr()[ac][:, lv]
     Cm = S.C.tocsr()[ac][:, ac]
     top = sp.hstack([sp.diags(mass), Bw.T])
