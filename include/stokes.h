@@ -113,6 +113,17 @@ stokes_status stokes_build_weights(stokes_ctx ctx, const double* phi_liquid, con
                                    const double* const* u_bc);
 
 /*
+ * Floor eps (0 <= eps <= 1, default 0) of the liquid fraction of live faces
+ * where it is the face's mass: from the next stokes_build_weights on, K =
+ * dt W_F / (rho max(W_L, eps)) and the velocity recovery and traction use
+ * the same floored fraction.  The paper (Section 5) is silent on slivers; a
+ * face holding a rounding-level amount of liquid otherwise makes K and the
+ * condition number arbitrarily large.  eps = 0 is the paper's system.
+ * STOKES_ERR_ARG outside [0, 1].
+ */
+stokes_status stokes_set_min_face_liquid(stokes_ctx ctx, double eps);
+
+/*
  * Unknown vectors use the context's internal "slot layout": every unknown
  * kind is stored on a padded copy of the (nx+1)(ny+1)(nz+1) vertex lattice,
  * one field after another (2D: tau_xx, tau_xy, p; 3D: tau_xx, tau_yy,
@@ -209,6 +220,40 @@ void stokes_default_options(stokes_options* o);
  */
 stokes_status stokes_traction_u_star(stokes_ctx ctx, const double* const* tau_bc, const double* p_bc,
                                      const double* const* u_star, double* const* u_star_out);
+
+/*
+ * Transport stage of the fractional-step Navier-Stokes routine around the
+ * implicit Stokes step (Section "Application to Viscous Jet Buckling"), 2D
+ * only: from u^n build u* = (first-order semi-Lagrangian advection of u^n
+ * with bilinear interpolation) + dt * gravity, and advect the liquid level
+ * set with the same velocity (basic semi-Lagrangian level set).
+ *   u_in[d], u_out[d] : u^n and u* per face kind, FP64 device, field layout;
+ *                       u_out may equal u_in (the velocity is staged)
+ *   phi_in, phi_out   : liquid level set on the half lattice (FP64 device);
+ *                       phi_in NULL skips the level set; phi_out must not
+ *                       overlap phi_in
+ *   gravity[2]        : body acceleration (host), added as dt * gravity
+ *   ext_passes        : Jacobi sweeps extending the velocity into faces that
+ *                       are not valid: each sweep gives such a face the mean
+ *                       of its valid 4-neighbours of the same component (left,
+ *                       right, below, above) and makes it valid
+ *   valid             : one byte per face (u then v, field layout, nonzero =
+ *                       valid), or NULL: valid faces are then those that are
+ *                       not fluid-without-liquid in the weights last built on
+ *                       this context (live faces and faces holding u_BC)
+ *   phi_union         : NULL, or a half-lattice level set of a source region
+ *                       (an inflow): phi_out = min(advected phi, phi_union)
+ * Positions are in grid units: u face (i, j) at (i, j + 1/2), v face (i, j)
+ * at (i + 1/2, j), lattice point (a, b) at ((a - 1)/2, (b - 1)/2); a
+ * departure point X - (dt/h) u(X) outside a field's samples is clamped onto
+ * them.  dt and h are the context's.  Enqueued on the context's stream; the
+ * first call allocates (nu + nv) * 18 bytes of scratch on the context.
+ * Errors: STOKES_ERR_ARG (3D, nx or ny < 2, null or aliased arrays),
+ * STOKES_ERR_STATE (valid NULL before any weight build), STOKES_ERR_CUDA.
+ */
+stokes_status stokes_advect(stokes_ctx ctx, const double* const* u_in, const double* phi_in, const double* gravity,
+                            int ext_passes, const uint8_t* valid, const double* phi_union, double* const* u_out,
+                            double* phi_out);
 
 /*
  * One implicit step (the hot path): b from u*, solve A x = b to the

@@ -20,6 +20,10 @@ cudaError_t bench_schwarz_kernels(Ctx* c, int launches, double* ms_local, double
 cudaError_t apply_preconditioner(Ctx* c, int which, const float* r, float* z);
 cudaError_t apply_schwarz_noalloc(Ctx* c, const float* r, float* z, std::string* why);
 double schwarz_setup_ms(Ctx* c);
+size_t advect_scratch_bytes(const Layout& L);
+cudaError_t launch_advect2d(Ctx* c, void* scratch, const double* const* u_in, const double* phi_in, const double* g,
+                            int passes, const uint8_t* valid, const double* phi_union, double* const* u_out,
+                            double* phi_out);
 }  // namespace stk
 
 extern "C" stokes_status stokes_apply_preconditioner(stokes_ctx h, int which, const float* r, float* z) {
@@ -260,6 +264,13 @@ stokes_status stokes_vector_layout(stokes_ctx h, stokes_layout* out) {
     return STOKES_OK;
 }
 
+stokes_status stokes_set_min_face_liquid(stokes_ctx h, double eps) {
+    if (!h) return STOKES_ERR_ARG;
+    if (!(eps >= 0.0 && eps <= 1.0)) { h->c.err = "min_face_liquid must lie in [0, 1]"; return STOKES_ERR_ARG; }
+    h->c.min_face_liquid = eps;
+    return STOKES_OK;
+}
+
 stokes_status stokes_build_weights(stokes_ctx h, const double* phiL, const double* phiS, const double* const* rho,
                                    const double* const* mu, const double* const* ubc) {
     if (!h) return STOKES_ERR_ARG;
@@ -383,6 +394,27 @@ stokes_status stokes_traction_u_star(stokes_ctx h, const double* const* tau_bc, 
     fields[c.nf - 1] = p_bc;
     if (!c.have_weights) { c.err = "stokes_build_weights has not run"; return STOKES_ERR_STATE; }
     API_CHECK_CUDA(h, launch_traction(&c, fields, u_star, u_star_out));
+    return STOKES_OK;
+}
+
+stokes_status stokes_advect(stokes_ctx h, const double* const* u_in, const double* phi_in, const double* gravity,
+                            int ext_passes, const uint8_t* valid, const double* phi_union, double* const* u_out,
+                            double* phi_out) {
+    if (!h) return STOKES_ERR_ARG;
+    Ctx& c = h->c;
+    if (c.L.dim != 2) { c.err = "stokes_advect is 2D only"; return STOKES_ERR_ARG; }
+    if (c.L.nx < 2 || c.L.ny < 2) { c.err = "stokes_advect needs nx, ny >= 2"; return STOKES_ERR_ARG; }
+    if (!u_in || !u_out || !gravity || ext_passes < 0) { c.err = "null argument or negative pass count"; return STOKES_ERR_ARG; }
+    for (int d = 0; d < 2; ++d)
+        if (!u_in[d] || !u_out[d]) { c.err = "null face component"; return STOKES_ERR_ARG; }
+    if (phi_in && (!phi_out || phi_out == phi_in)) {
+        c.err = "phi_out must be a device array distinct from phi_in";
+        return STOKES_ERR_ARG;
+    }
+    if (!valid && !c.have_weights) { c.err = "no validity mask and stokes_build_weights has not run"; return STOKES_ERR_STATE; }
+    if (!c.adv_scratch) API_CHECK_CUDA(h, dalloc(c, &c.adv_scratch, advect_scratch_bytes(c.L)));
+    API_CHECK_CUDA(h, launch_advect2d(&c, c.adv_scratch, u_in, phi_in, gravity, ext_passes, valid, phi_union, u_out,
+                                      phi_out));
     return STOKES_OK;
 }
 

@@ -61,6 +61,7 @@ struct Ctx {
     int* tiles = nullptr;       // active tile list (device)
     int* d_ntiles = nullptr;
     bool have_weights = false;
+    double min_face_liquid = 0.0;   // floor of the live faces' mass fraction (next weight build)
     bool own_stream = false;
     std::vector<void*> allocs;
     DevArrays A{};
@@ -86,6 +87,8 @@ struct Ctx {
     std::vector<void*> sw_allocs;
     bool sw_ready = false;
     double sw_setup_ms = 0.0;
+    // transport step (advect.cu): staged velocity and validity, allocated on first use
+    void* adv_scratch = nullptr;
 
     DevArrays dev_arrays() const { return A; }
     cudaError_t zero_weights() { return cudaMemsetAsync(weight_block, 0, weight_bytes, stream); }

@@ -313,8 +313,10 @@ __device__ __forceinline__ bool zwm(const DevArrays& D, int kind, int64_t o) {
 //   3D u: cells (i-1),(i); exy (i,j),(i,j+1); exz (i,j,k),(i,j,k+1)
 //   3D v: cells (j-1),(j); exy (i,j),(i+1,j); eyz (i,j,k),(i,j,k+1)
 //   3D w: cells (k-1),(k); exz (i,j,k),(i+1,j,k); eyz (i,j,k),(i,j+1,k)
-__global__ void k_faces2d(Layout L, double dt, const double* rho_u, const double* rho_v, const double* ubc_u,
-                          const double* ubc_v, DevArrays D) {
+// wl_min floors the liquid fraction of live faces where it is their mass
+// (K and the recovery coefficient); 0 keeps the fractions as computed.
+__global__ void k_faces2d(Layout L, double dt, double wl_min, const double* rho_u, const double* rho_v,
+                          const double* ubc_u, const double* ubc_v, DevArrays D) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i > L.nx || j > L.ny) return;
@@ -340,8 +342,9 @@ __global__ void k_faces2d(Layout L, double dt, const double* rho_u, const double
         if (wf > 0.0 && wl > 0.0) {
             fl |= F_LIVE;
             double rho = (d == 0 ? rho_u : rho_v)[fidx2(kind, i, j, L.nx, L.ny)];
-            K = (dt * wf) / (rho * wl);
-            rec = dt / (rho * wl);
+            double wm = fmax(wl, wl_min);
+            K = (dt * wf) / (rho * wm);
+            rec = dt / (rho * wm);
         } else if (wf > 0.0) {
             fl |= F_BAD;
         }
@@ -353,7 +356,7 @@ __global__ void k_faces2d(Layout L, double dt, const double* rho_u, const double
     }
 }
 
-__global__ void k_faces3d(Layout L, double dt, Ptr3 rho, Ptr3 ubc, DevArrays D) {
+__global__ void k_faces3d(Layout L, double dt, double wl_min, Ptr3 rho, Ptr3 ubc, DevArrays D) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
     int k = blockIdx.z;
@@ -388,8 +391,9 @@ __global__ void k_faces3d(Layout L, double dt, Ptr3 rho, Ptr3 ubc, DevArrays D) 
         if (wf > 0.0 && wl > 0.0) {
             fl |= F_LIVE;
             double r = rho.p[d][fi];
-            K = (dt * wf) / (r * wl);
-            rec = dt / (r * wl);
+            double wm = fmax(wl, wl_min);
+            K = (dt * wf) / (r * wm);
+            rec = dt / (r * wm);
         } else if (wf > 0.0) {
             fl |= F_BAD;
         }
@@ -648,7 +652,7 @@ cudaError_t launch_build_weights(Ctx* c, const double* phiL, const double* phiS,
     if (L.dim == 2) {
         dim3 grd((L.nx + 1 + 31) / 32, (L.ny + 1 + 7) / 8);
         k_fractions2d<<<grd, blk, 0, s>>>(L, phiL, phiS, D);
-        k_faces2d<<<grd, blk, 0, s>>>(L, c->g.dt, rho[0], rho[1], ubc[0], ubc[1], D);
+        k_faces2d<<<grd, blk, 0, s>>>(L, c->g.dt, c->min_face_liquid, rho[0], rho[1], ubc[0], ubc[1], D);
         k_unknowns2d<<<grd, blk, 0, s>>>(L, 1.0 / c->g.h, mu[0], mu[1], D);
         k_finish2d<<<grd, blk, 0, s>>>(L, D);
     } else {
@@ -656,7 +660,7 @@ cudaError_t launch_build_weights(Ctx* c, const double* phiL, const double* phiS,
         Ptr3 r3{{rho[0], rho[1], rho[2]}}, u3{{ubc[0], ubc[1], ubc[2]}};
         Ptr4 m4{{mu[0], mu[1], mu[2], mu[3]}};
         k_fractions3d<<<grd, blk, 0, s>>>(L, phiL, phiS, D);
-        k_faces3d<<<grd, blk, 0, s>>>(L, c->g.dt, r3, u3, D);
+        k_faces3d<<<grd, blk, 0, s>>>(L, c->g.dt, c->min_face_liquid, r3, u3, D);
         k_unknowns3d<<<grd, blk, 0, s>>>(L, 1.0 / c->g.h, m4, D);
         k_finish3d<<<grd, blk, 0, s>>>(L, D);
     }

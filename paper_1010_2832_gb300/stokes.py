@@ -53,7 +53,8 @@ EXPORTED = ("stokes_create", "stokes_destroy", "stokes_last_error", "stokes_buil
             "stokes_net_gradient", "stokes_net_train_step", "stokes_set_learned_preconditioner",
             "stokes_learned_grid", "stokes_learned_features", "stokes_learned_targets",
             "stokes_learned_jacobi_steps", "stokes_apply_preconditioner", "stokes_schwarz_setup_ms",
-            "stokes_apply_schwarz_noalloc", "stokes_bench_schwarz_kernels", "stokes_traction_u_star")
+            "stokes_apply_schwarz_noalloc", "stokes_bench_schwarz_kernels", "stokes_traction_u_star",
+            "stokes_advect", "stokes_set_min_face_liquid")
 
 
 class BatchIO(C.Structure):
@@ -116,6 +117,8 @@ def load_library(path=LIB_PATH):
         "stokes_apply_schwarz_noalloc": (I, [P, P, P]),
         "stokes_bench_schwarz_kernels": (I, [P, I, C.POINTER(D), C.POINTER(D), C.POINTER(D)]),
         "stokes_traction_u_star": (I, [P, PP, P, PP, PP]),
+        "stokes_advect": (I, [P, PP, P, C.POINTER(D), I, P, P, PP, P]),
+        "stokes_set_min_face_liquid": (I, [P, D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -203,6 +206,11 @@ class StokesContext:
                                                   rp, mp, up))
 
     # ---- vectors -----------------------------------------------------------
+    def set_min_face_liquid(self, eps):
+        """Floor of the live faces' mass fraction from the next weight build
+        (stokes_set_min_face_liquid); 0 is the paper's system."""
+        self._check(self.lib.stokes_set_min_face_liquid(self.h, float(eps)))
+
     def new_vector(self, dtype=torch.float64):
         return torch.zeros(self.layout.total, dtype=dtype, device="cuda")
 
@@ -237,6 +245,21 @@ class StokesContext:
         up, ua = _ptrs([_dev(t) for t in u_star])
         op, oa = _ptrs([_dev(t) for t in u_star_out])
         self._check(self.lib.stokes_traction_u_star(self.h, tp, _dev(p_bc).data_ptr(), up, op))
+
+    def advect(self, u_in, u_out, gravity, ext_passes=0, phi_in=None, phi_out=None, valid=None, phi_union=None):
+        """Transport stage around the Stokes step (stokes_advect): u_out <- u*,
+        phi_out <- advected level set; FP64 device tensors, valid a uint8
+        device tensor (u then v faces) or None for the context's weights."""
+        up, ua = _ptrs([_dev(t) for t in u_in])
+        op, oa = _ptrs([_dev(t) for t in u_out])
+        g = (C.c_double * 2)(*[float(x) for x in gravity])
+        ptr = lambda t: None if t is None else t.data_ptr()
+        if valid is not None and (valid.dtype != torch.uint8 or not valid.is_cuda):
+            raise TypeError("valid must be a uint8 device tensor")
+        self._check(self.lib.stokes_advect(self.h, up, ptr(None if phi_in is None else _dev(phi_in)),
+                                           g, int(ext_passes), ptr(valid),
+                                           ptr(None if phi_union is None else _dev(phi_union)), op,
+                                           ptr(None if phi_out is None else _dev(phi_out))))
 
     def solve_step(self, u_star, u_out, tau_out, p_out, options=None):
         o = options or default_options()
@@ -495,9 +518,12 @@ def upload_workload(wl):
                 mu=[t(a) for a in wl.mu], u_bc=[t(a) for a in wl.u_bc], u_star=[t(a) for a in wl.u_star])
 
 
-def context_for(wl, stream=None):
-    """Create a context for a workload and build its weights on the device."""
+def context_for(wl, stream=None, min_face_liquid=0.0):
+    """Create a context for a workload and build its weights on the device
+    (with the given floor of the live faces' mass fraction)."""
     ctx = StokesContext(wl.dim, wl.n, wl.h, wl.dt, wl.origin, stream=stream)
+    if min_face_liquid:
+        ctx.set_min_face_liquid(min_face_liquid)
     d = upload_workload(wl)
     ctx.build_weights(d["phi_liquid"], d["phi_solid"], d["rho"], d["mu"], d["u_bc"])
     return ctx, d

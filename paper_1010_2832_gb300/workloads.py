@@ -144,6 +144,50 @@ def paper_annulus(n):
                           lambda P: 1.0, lambda P: 0.1, lambda d, P: 0.0, _smooth_ustar)
 
 
+# Planar jet buckling (Section "Two Dimensional Jet Buckling")
+JET2D = dict(center=(0.5, 0.5), radius=0.4, ceiling=0.8, jet_x=0.5, width=0.06, U=-0.5,
+             rho=1.0, mu=0.075, g=(0.0, -9.81))
+
+
+def _jet_opening_phi(X, h, depth):
+    """< 0 inside the jet opening [x0 - D/2, x0 + D/2] x [ceiling - depth, inf)."""
+    J = JET2D
+    half = J["width"] / 2
+    return np.maximum(np.abs(X[0] - J["jet_x"]) - half, (J["ceiling"] - depth) - X[1])
+
+
+def jet_2d(n=150, dt=0.002, stub_cells=3):
+    """Planar viscous jet: n x n grid on the unit square; solid outside the
+    circle of radius 0.4 centred at (0.5, 0.5) and above the ceiling
+    y = 0.8; the part of the ceiling over the opening of width D = 0.06 at
+    x = 0.5 moves with u_BC = (0, U), U = -0.5 (the inflow), its profile
+    ramped linearly over one cell at the opening's edges so that the v faces
+    carry the flux D U exactly; rho = 1, mu = 0.075.  The liquid starts as a
+    stub of ``stub_cells`` cells below the opening (and fills the opening);
+    u* = (0, U) everywhere (the initial velocity)."""
+    J = JET2D
+    h = 1.0 / n
+    def phiS(X):
+        r = np.hypot(X[0] - J["center"][0], X[1] - J["center"][1])
+        return np.minimum(J["radius"] - r, J["ceiling"] - X[1])
+    def ubc(d, P):
+        if d == 0:
+            return np.zeros(P[0].shape)
+        ramp = np.clip((J["width"] / 2 - np.abs(P[0] - J["jet_x"])) / h + 0.5, 0.0, 1.0)
+        return J["U"] * ramp * (P[1] >= J["ceiling"] - h / 4)
+    return from_functions(f"jet{n}", 2, (n, n), h, dt, (0.0, 0.0),
+                          lambda X: _jet_opening_phi(X, h, stub_cells * h), phiS,
+                          lambda P: J["rho"], lambda P: J["mu"], ubc,
+                          lambda d, P: np.full(P[0].shape, 0.0 if d == 0 else J["U"]))
+
+
+def jet_2d_source(n=150):
+    """Half-lattice level set of the jet opening (the inflow source region):
+    the liquid level set is united with it after every advection."""
+    h = 1.0 / n
+    return np.ascontiguousarray(_jet_opening_phi(lattice_points((n, n), h, (0.0, 0.0)), h, 0.0))
+
+
 def _bumps(rng, dim, k=8, c_lo=0.2, c_hi=0.8, s_lo=0.05, s_hi=0.12):
     c = rng.uniform(c_lo, c_hi, (k, dim))
     s = rng.uniform(s_lo, s_hi, k)
