@@ -144,6 +144,27 @@ def paper_annulus(n):
                           lambda P: 1.0, lambda P: 0.1, lambda d, P: 0.0, _smooth_ustar)
 
 
+def sphere_3d(n, half=1.25):
+    """The 3D case of Section 9 (Three Dimensional Stokes Flow): a liquid
+    sphere r < 1 at the origin with a free surface, a static solid sphere
+    r < 0.25 inside it, rho = 1, mu = 0.1, dt = 1, and the printed input
+    velocity u = (0.5 + x sin(yz), cos(y/4) + xyz/2, x + yz^2/2 + sqrt(2 + y^2)).
+    The box is [-half, half]^3 (the paper does not state it), n^3 cells."""
+    h = 2.0 * half / n
+    lo, hi = (-half,) * 3, (half,) * 3
+    def ustar(d, P):
+        x, y, z = P
+        if d == 0:
+            return 0.5 + x * np.sin(y * z)
+        if d == 1:
+            return np.cos(0.25 * y) + 0.5 * x * y * z
+        return x + 0.5 * y * z * z + np.sqrt(2.0 + y * y)
+    R = lambda X: np.sqrt(X[0] ** 2 + X[1] ** 2 + X[2] ** 2)
+    return from_functions(f"sphere{n}", 3, (n, n, n), h, 1.0, lo,
+                          lambda X: R(X) - 1.0, lambda X: np.minimum(box_phi(X, lo, hi), R(X) - 0.25),
+                          lambda P: 1.0, lambda P: 0.1, lambda d, P: 0.0, ustar)
+
+
 # Planar jet buckling (Section "Two Dimensional Jet Buckling")
 JET2D = dict(center=(0.5, 0.5), radius=0.4, ceiling=0.8, jet_x=0.5, width=0.06, U=-0.5,
              rho=1.0, mu=0.075, g=(0.0, -9.81))
