@@ -145,7 +145,7 @@ __device__ void tile_report(double v0, double v1, double* part, int w, BState* s
 // FP64 (alpha = 0 outside a CG step).  Thread 0 starts the bulk copy of the
 // factor and waits on the CTA's mbarrier (phase parity = uses & 1, bounded);
 // a copy that never completes sets the batch's error flag.
-__device__ void batched_local_solve(const BInst& I, int p, double alpha, float* Xs, float* s, float* y,
+__device__ void batched_local_solve(const BInst& I, int p, double alpha, uint8_t* Fs, float* s, float* y,
                                     unsigned long long* bar, uint32_t& uses, int& ok_s, BGlobal* g) {
     const SchwarzPlan& P = I.sw;
     const Layout& L = I.L;
@@ -157,7 +157,7 @@ __device__ void batched_local_solve(const BInst& I, int p, double alpha, float* 
     if (!ok_s) return;
     const int n = P.nloc[p];
     const uint32_t b_addr = smem_u32(bar);
-    if (t == 0) sw_issue(b_addr, Xs, P.inv + (int64_t)p * PFAC, (uint32_t)(tri4_off(n) * (int)sizeof(float)));
+    if (t == 0) sw_issue(b_addr, Fs, P.fac + (int64_t)p * SW_FAC_BYTES, sw_patch_bytes(n));
     constexpr float H = 0.70710678118654752f;
     const int CI = P.corner[p] & 0xffff, CJ = P.corner[p] >> 16;
     const int a0 = PB * CI - 1, b0 = PB * CJ - 1;
@@ -189,7 +189,7 @@ __device__ void batched_local_solve(const BInst& I, int p, double alpha, float* 
             }
         }
     }
-    if (t >= n && t < (n + 3) / 4 * 4) s[t] = 0.f;
+    if (t >= n && t < (n + 7) / 8 * 8) s[t] = 0.f;
     if (t == 0) {
         ok_s = mbar_wait(b_addr, uses & 1u) ? 1 : 0;
         ++uses;
@@ -203,41 +203,7 @@ __device__ void batched_local_solve(const BInst& I, int p, double alpha, float* 
         __syncthreads();
         return;
     }
-    if (t < n) {
-        const float* xr = Xs + tri4_off(t);
-        const float4* s4 = reinterpret_cast<const float4*>(s);
-        float acc = 0.f;
-        for (int j = 0; j <= t / 4; ++j) {
-            const float4 a = *reinterpret_cast<const float4*>(xr + 4 * j), b = s4[j];
-            acc = fmaf(a.x, b.x, acc);
-            acc = fmaf(a.y, b.y, acc);
-            acc = fmaf(a.z, b.z, acc);
-            acc = fmaf(a.w, b.w, acc);
-        }
-        y[t] = acc;
-    }
-    __syncthreads();
-    {
-        const int cb = t >> 2, q = t & 3;
-        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (4 * cb < n)
-            for (int row = 4 * cb + q; row < n; row += 4) {
-                const float4 a = *reinterpret_cast<const float4*>(Xs + tri4_off(row) + 4 * cb);
-                const float yr = y[row];
-                z.x = fmaf(a.x, yr, z.x);
-                z.y = fmaf(a.y, yr, z.y);
-                z.z = fmaf(a.z, yr, z.z);
-                z.w = fmaf(a.w, yr, z.w);
-            }
-        for (int o = 1; o <= 2; o <<= 1) {
-            z.x += __shfl_xor_sync(0xffffffffu, z.x, o);
-            z.y += __shfl_xor_sync(0xffffffffu, z.y, o);
-            z.z += __shfl_xor_sync(0xffffffffu, z.z, o);
-            z.w += __shfl_xor_sync(0xffffffffu, z.w, o);
-        }
-        if (q == 0 && 4 * cb < n) reinterpret_cast<float4*>(s)[cb] = z;
-    }
-    __syncthreads();
+    sw_factor_products(Fs, n, s, y);
     float* out = P.ybuf + (int64_t)(CJ * P.npx + CI) * PMAX;
     if (t < 2 * PR * PR) {
         const int e = t;
@@ -277,7 +243,7 @@ __device__ __forceinline__ double batched_gather(const BInst& I, int f, int i, i
 template <int TY, bool SW>
 struct BatchedSmem {
     static constexpr int APPLY = (int)sizeof(Smem2<double, TY>);
-    static constexpr int LOCAL = SW ? PFAC * (int)sizeof(float) : 0;
+    static constexpr int LOCAL = SW ? SW_FAC_BYTES : 0;
     static constexpr int BYTES = APPLY > LOCAL ? APPLY : LOCAL;
 };
 
@@ -292,8 +258,8 @@ __global__ void __launch_bounds__(256) k_batched(const BInst* __restrict__ inst,
     // factor (phase C) never live at the same time
     __shared__ __align__(128) unsigned char smraw[BatchedSmem<TY, SW>::BYTES];
     Smem2<double, TY>& sm = *reinterpret_cast<Smem2<double, TY>*>(smraw);
-    float* Xs = reinterpret_cast<float*>(smraw);
-    __shared__ __align__(16) float ls[SW ? PMAX : 4];
+    uint8_t* Fs = reinterpret_cast<uint8_t*>(smraw);
+    __shared__ __align__(16) float ls[SW ? PMAX8 : 4];
     __shared__ float ly[SW ? PMAX : 4];
     __shared__ __align__(8) unsigned long long lbar;
     __shared__ int lok;
@@ -368,7 +334,7 @@ __global__ void __launch_bounds__(256) k_batched(const BInst* __restrict__ inst,
                 volatile BState* vs = st + i;
                 if (vs->done) continue;
                 const double alpha = vs->mode == 0 ? vs->alpha : 0.0;
-                batched_local_solve(inst[i], pl_patch[k], alpha, Xs, ls, ly, &lbar, uses, lok, g);
+                batched_local_solve(inst[i], pl_patch[k], alpha, Fs, ls, ly, &lbar, uses, lok, g);
             }
             if (!grid_sync(g, nb)) return;
         }
@@ -452,7 +418,7 @@ struct stokes_batch_s {
     bool sw = false;            // additive Schwarz preconditioner for every instance
     int* d_pl = nullptr;        // [2][pl_cap]: instance, patch
     int npatch = 0, pl_cap = 0;
-    std::vector<const float*> plan_key;   // each instance's factor pointer when the plan was uploaded
+    std::vector<const uint8_t*> plan_key; // each instance's factor pointer when the plan was uploaded
     stokes_options opt{};
     cudaStream_t s = nullptr;
     int ty = 8, cps = 1;        // chosen tile height and CTAs per SM
@@ -543,7 +509,7 @@ static cudaError_t upload_patches(stokes_batch b, const std::vector<BInst>& inst
     if (!b->sw) { b->npatch = 0; return cudaSuccess; }
     std::vector<int> pi, pp;
     for (int i = 0; i < b->n; ++i) {
-        b->plan_key[i] = insts[i].sw.inv;
+        b->plan_key[i] = insts[i].sw.fac;
         if (insts[i].te == insts[i].tb) continue;        // no active tile: retired at once
         for (int q = 0; q < insts[i].sw.np; ++q) { pi.push_back(i); pp.push_back(q); }
     }
@@ -861,7 +827,7 @@ stokes_status stokes_batch_solve(stokes_batch b, const stokes_batch_io* io, stok
         for (int i = 0; i < b->n; ++i) {
             const SchwarzPlan* P = nullptr;
             if ((e = schwarz_ensure(b->c[i], &P)) != cudaSuccess) return STOKES_ERR_CUDA;
-            moved |= (int)b->plan_key.size() != b->n || P->inv != b->plan_key[i];
+            moved |= (int)b->plan_key.size() != b->n || P->fac != b->plan_key[i];
         }
         if (moved && (e = upload_plan(b, b->ty)) != cudaSuccess) return STOKES_ERR_CUDA;
     }

@@ -290,7 +290,7 @@ static cudaError_t schwarz_build(Ctx* c) {
     if ((e = al((void**)&P.lmap, sizeof(short) * np * PMAX)) != cudaSuccess) return e;
     // FP32 factors: BF16 storage halves the local-solve traffic but, measured
     // on the 1024^2 bump workload, needs 4.4x the CG iterations
-    if ((e = al((void**)&P.inv, sizeof(float) * np * PFAC)) != cudaSuccess) return e;
+    if ((e = al((void**)&P.fac, (size_t)SW_FAC_BYTES * np)) != cudaSuccess) return e;
     if ((e = al((void**)&P.scale, sizeof(float) * np * PMAX)) != cudaSuccess) return e;
     if ((e = al((void**)&P.ybuf, sizeof(float) * ng * PMAX)) != cudaSuccess) return e;
     cudaMemcpyAsync(P.pid, pid.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, c->stream);
@@ -892,7 +892,7 @@ cudaError_t bench_schwarz_kernels(Ctx* c, int launches, double* ms_local, double
         return e;
     double by = 0.0;
     for (int q = 0; q < P.np; ++q)
-        by += (double)tri4_off(nloc[q]) * sizeof(float) + PMAX * (sizeof(float) + sizeof(float) + sizeof(short)) +
+        by += (double)sw_patch_bytes(nloc[q]) + PMAX * (sizeof(float) + sizeof(float) + sizeof(short)) +
               2 * PR * PR * sizeof(float) + 2 * sizeof(int);
     *bytes_local = by;
     if ((e = push_inner_params(c, 1.0, 0.0, 1 << 30)) != cudaSuccess) return e;

@@ -249,42 +249,41 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
         }
         __syncthreads();
     }
-    // packed rows of X (row r: X[r][0..r], padded to 16 bytes) and the
-    // scaling by position.  The patch operator D^-1/2 X^T X D^-1/2 is
-    // symmetric positive definite whatever the rounding of X (X stays
-    // triangular with a positive diagonal).
-    const int n4 = (n + 3) / 4 * 4;
-    for (int e = t; e < n * n4; e += 256) {
-        int r = e / n4, c = e % n4;
-        if (c < (r / 4 + 1) * 4) {
-            P.inv[(int64_t)p * PFAC + tri4_off(r) + c] = c <= r ? X[r * PMAX + c] : 0.f;
-        }
+    // stored factor: row factors rho_r^2 and the packed FP16 rows X[r][0..r] /
+    // rho_r (padded to 16 bytes), and the scaling by position.  The patch
+    // operator D^-1/2 X~^T diag(rho^2) X~ D^-1/2 is symmetric positive
+    // definite whatever the rounding of X~ (it stays triangular with a
+    // positive diagonal: |X[r][r]| >= 1 and rho_r <= sqrt(cond)).
+    __shared__ float rho_inv[PMAX];
+    uint8_t* F = P.fac + (int64_t)p * SW_FAC_BYTES;
+    if (t < PMAX) {
+        float m = 0.f;
+        if (t < n)
+            for (int c = 0; c <= t; ++c) m = fmaxf(m, fabsf(X[t * PMAX + c]));
+        rho_inv[t] = m > 0.f ? 1.f / m : 0.f;
+        reinterpret_cast<float*>(F)[t] = m * m;
+    }
+    __syncthreads();
+    __half* Xh = reinterpret_cast<__half*>(F + SW_RS_BYTES);
+    const int n8 = (n + 7) / 8 * 8;
+    for (int e = t; e < n * n8; e += 256) {
+        const int r = e / n8, c = e % n8;
+        if (c < (r / 8 + 1) * 8) Xh[tri8_off(r) + c] = __float2half_rn(c <= r ? X[r * PMAX + c] * rho_inv[r] : 0.f);
     }
     for (int e = t; e < PMAX; e += 256) P.scale[(int64_t)p * PMAX + e] = map[e] >= 0 ? sc[map[e]] : 0.f;
 }
 
-// Bytes of patch p's packed factor (a multiple of 16).
-__device__ __forceinline__ uint32_t sw_bytes(const SchwarzPlan& P, int p) {
-    return (uint32_t)(tri4_off(P.nloc[p]) * (int)sizeof(float));      // a multiple of 16
-}
-
-// four consecutive stored entries (one 16-byte load)
-__device__ __forceinline__ float4 ld4(const float* x) { return *reinterpret_cast<const float4*>(x); }
-
-// z_p = Q D^-1/2 X^T X D^-1/2 Q r_p with X = L^-1, one CTA (128 threads)
-// per active patch.  Thread 0 starts a bulk (TMA) copy of the packed factor
-// into shared memory, completing on an mbarrier; meanwhile the threads
-// gather, rotate and scale r_p into s.  Then y = X s (thread t: row t,
-// 16-byte loads of the padded rows) and z = X^T y (four threads per block of
-// four columns, each taking every fourth row, joined by shuffles); rotate
-// back and store by position.  About 25 KB of shared memory per CTA, so
-// eight CTAs share an SM and their copies overlap each other's arithmetic.
-// A copy that never completes (bounded wait) marks the solve
-// STOKES_ERR_TIMEOUT and ends it.
+// z_p = Q D^-1/2 X~^T diag(rho^2) X~ D^-1/2 Q r_p, one CTA (128 threads) per
+// active patch.  Thread 0 starts a bulk (TMA) copy of the stored factor
+// (13 KB at most) into shared memory, completing on an mbarrier; meanwhile
+// the threads gather, rotate and scale r_p into s.  Then the two triangular
+// products (sw_factor_products); rotate back and store by position.  A copy
+// that never completes (bounded wait) marks the solve STOKES_ERR_TIMEOUT and
+// ends it.
 __global__ void __launch_bounds__(128) k_schwarz_gemv(Layout L, SchwarzPlan P, const float* __restrict__ r,
                                                       CgScalars* sc) {
-    extern __shared__ __align__(128) float Xs[];               // PFAC floats
-    __shared__ __align__(16) float s[PMAX];
+    extern __shared__ __align__(128) uint8_t Fs[];             // SW_FAC_BYTES
+    __shared__ __align__(16) float s[PMAX8];
     __shared__ float y[PMAX];
     __shared__ __align__(8) unsigned long long bar;
     __shared__ int ok_s;
@@ -292,13 +291,13 @@ __global__ void __launch_bounds__(128) k_schwarz_gemv(Layout L, SchwarzPlan P, c
     const int t = threadIdx.x;
     const int p = blockIdx.x;
     const uint32_t b_addr = smem_u32(&bar);
+    const int n = P.nloc[p];
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_addr), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        sw_issue(b_addr, Xs, P.inv + (int64_t)p * PFAC, sw_bytes(P, p));
+        sw_issue(b_addr, Fs, P.fac + (int64_t)p * SW_FAC_BYTES, sw_patch_bytes(n));
     }
     constexpr float H = 0.70710678118654752f;
-    const int n = P.nloc[p];
     const int I = P.corner[p] & 0xffff, J = P.corner[p] >> 16;
     const int a0 = PB * I - 1, b0 = PB * J - 1;
     const short* map = P.lmap + (int64_t)p * PMAX;
@@ -333,7 +332,7 @@ __global__ void __launch_bounds__(128) k_schwarz_gemv(Layout L, SchwarzPlan P, c
             }
         }
     }
-    if (t >= n && t < (n + 3) / 4 * 4) s[t] = 0.f;    // the padded last block
+    if (t >= n && t < (n + 7) / 8 * 8) s[t] = 0.f;    // the padded last block
     if (t == 0) ok_s = mbar_wait(b_addr, 0) ? 1 : 0;
     __syncthreads();
     if (!ok_s) {
@@ -345,45 +344,7 @@ __global__ void __launch_bounds__(128) k_schwarz_gemv(Layout L, SchwarzPlan P, c
         }
         return;
     }
-    const float* X = Xs;
-    if (t < n) {
-        const float* xr = X + tri4_off(t);
-        const float4* s4 = reinterpret_cast<const float4*>(s);
-        float acc = 0.f;
-        for (int j = 0; j <= t / 4; ++j) {
-            const float4 a = ld4(xr + 4 * j), b = s4[j];
-            acc = fmaf(a.x, b.x, acc);
-            acc = fmaf(a.y, b.y, acc);
-            acc = fmaf(a.z, b.z, acc);
-            acc = fmaf(a.w, b.w, acc);
-        }
-        y[t] = acc;
-    }
-    __syncthreads();
-    // z = X^T y: column block cb = t / 4 (columns 4cb..4cb+3), rows
-    // r = 4cb + (t % 4) + 4i; the four partial sums meet by shuffles
-    {
-        const int cb = t >> 2, q = t & 3;
-        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (4 * cb < n)
-            for (int row = 4 * cb + q; row < n; row += 4) {
-                const float4 a = ld4(X + tri4_off(row) + 4 * cb);
-                const float yr = y[row];
-                z.x = fmaf(a.x, yr, z.x);
-                z.y = fmaf(a.y, yr, z.y);
-                z.z = fmaf(a.z, yr, z.z);
-                z.w = fmaf(a.w, yr, z.w);
-            }
-        for (int o = 1; o <= 2; o <<= 1) {
-            z.x += __shfl_xor_sync(0xffffffffu, z.x, o);
-            z.y += __shfl_xor_sync(0xffffffffu, z.y, o);
-            z.z += __shfl_xor_sync(0xffffffffu, z.z, o);
-            z.w += __shfl_xor_sync(0xffffffffu, z.w, o);
-        }
-        // s is no longer read (y = X s ended at the barrier above)
-        if (q == 0 && 4 * cb < n) reinterpret_cast<float4*>(s)[cb] = z;
-    }
-    __syncthreads();
+    sw_factor_products(Fs, n, s, y);
     // scale, rotate back and store by position
     float* out = P.ybuf + (int64_t)(J * P.npx + I) * PMAX;
     if (t < 2 * PR * PR) {
@@ -402,8 +363,8 @@ __global__ void __launch_bounds__(128) k_schwarz_gemv(Layout L, SchwarzPlan P, c
     }
 }
 
-// dynamic shared memory of k_schwarz_gemv: the packed factor
-constexpr int SW_GEMV_SMEM = PFAC * (int)sizeof(float);
+// dynamic shared memory of k_schwarz_gemv: the stored factor
+constexpr int SW_GEMV_SMEM = SW_FAC_BYTES;
 
 static inline void launch_schwarz_gemv(const Layout& L, const SchwarzPlan& P, const float* r, CgScalars* sc,
                                        cudaStream_t s) {
