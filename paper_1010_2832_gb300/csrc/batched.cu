@@ -418,7 +418,7 @@ struct stokes_batch_s {
     bool sw = false;            // additive Schwarz preconditioner for every instance
     int* d_pl = nullptr;        // [2][pl_cap]: instance, patch
     int npatch = 0, pl_cap = 0;
-    std::vector<const uint8_t*> plan_key; // each instance's factor pointer when the plan was uploaded
+    std::vector<unsigned> plan_epoch;     // each instance's plan build count when its plan was uploaded
     stokes_options opt{};
     cudaStream_t s = nullptr;
     int ty = 8, cps = 1;        // chosen tile height and CTAs per SM
@@ -431,8 +431,9 @@ struct stokes_batch_s {
     BGlobal* d_g0 = nullptr;
     bool use_graph = true;
     BGlobal* d_g = nullptr;
-    int* d_wl = nullptr;        // [3][nwork]
-    double* d_part = nullptr;
+    int* d_wl = nullptr;        // [3][wl_cap]: instance, first column, first row of each work tile
+    double* d_part = nullptr;   // [2 wl_cap] per-tile partial sums
+    size_t wl_cap = 0;
     int nwork = 0;
     int grid = 0;
     std::vector<BState> h_st;
@@ -505,11 +506,11 @@ static cudaError_t build_worklist(stokes_batch b, int ty, std::vector<int>& wi, 
 // Patch list of the Schwarz phase (instance, patch), in instance order; a
 // larger list than the last one reallocates (and so needs a new graph).
 static cudaError_t upload_patches(stokes_batch b, const std::vector<BInst>& insts) {
-    b->plan_key.assign(b->n, nullptr);
+    b->plan_epoch.assign(b->n, 0u);
     if (!b->sw) { b->npatch = 0; return cudaSuccess; }
     std::vector<int> pi, pp;
     for (int i = 0; i < b->n; ++i) {
-        b->plan_key[i] = insts[i].sw.fac;
+        b->plan_epoch[i] = b->c[i]->sw_epoch;
         if (insts[i].te == insts[i].tb) continue;        // no active tile: retired at once
         for (int q = 0; q < insts[i].sw.np; ++q) { pi.push_back(i); pp.push_back(q); }
     }
@@ -537,6 +538,7 @@ static cudaError_t upload_plan(stokes_batch b, int ty) {
     std::vector<BInst> insts;
     cudaError_t e = build_worklist(b, ty, wi, wc, wr, insts);
     if (e != cudaSuccess) return e;
+    const int old_nwork = b->nwork;
     b->nwork = (int)wi.size();
     std::vector<BState> st0(b->n);
     std::memset(st0.data(), 0, st0.size() * sizeof(BState));
@@ -546,15 +548,26 @@ static cudaError_t upload_plan(stokes_batch b, int ty) {
     if ((e = cudaMemcpy(b->d_st0, st0.data(), st0.size() * sizeof(BState), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
     if ((e = cudaMemcpy(b->d_g0, &g0, sizeof(g0), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
-    if (b->d_wl) { cudaFree(b->d_wl); b->d_wl = nullptr; }
-    if (b->d_part) { cudaFree(b->d_part); b->d_part = nullptr; }
-    size_t nw = std::max(1, b->nwork);
-    if ((e = cudaMalloc(&b->d_wl, 3 * nw * sizeof(int))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&b->d_part, 2 * nw * sizeof(double))) != cudaSuccess) return e;
+    // A captured graph holds the work-list and partial-sum pointers, the work
+    // count and the grid by value: it is dropped whenever any of them changes
+    // (the next solve captures again).  The buffers keep their capacity.
+    const size_t need = std::max(1, b->nwork);
+    if (!b->d_wl || need > b->wl_cap) {
+        if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+        if (b->d_wl) { cudaFree(b->d_wl); b->d_wl = nullptr; }
+        if (b->d_part) { cudaFree(b->d_part); b->d_part = nullptr; }
+        b->wl_cap = need;
+        if ((e = cudaMalloc(&b->d_wl, 3 * b->wl_cap * sizeof(int))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&b->d_part, 2 * b->wl_cap * sizeof(double))) != cudaSuccess) return e;
+    }
+    if (b->nwork != old_nwork && b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     if (b->nwork) {
-        cudaMemcpy(b->d_wl, wi.data(), wi.size() * sizeof(int), cudaMemcpyHostToDevice);
-        cudaMemcpy(b->d_wl + nw, wc.data(), wc.size() * sizeof(int), cudaMemcpyHostToDevice);
-        cudaMemcpy(b->d_wl + 2 * nw, wr.data(), wr.size() * sizeof(int), cudaMemcpyHostToDevice);
+        const size_t nw = b->wl_cap;
+        if ((e = cudaMemcpy(b->d_wl, wi.data(), wi.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(b->d_wl + nw, wc.data(), wc.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(b->d_wl + 2 * nw, wr.data(), wr.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+            return e;
     }
     if ((e = upload_patches(b, insts)) != cudaSuccess) return e;
     return cudaMemcpy(b->d_inst, insts.data(), insts.size() * sizeof(BInst), cudaMemcpyHostToDevice);
@@ -566,7 +579,7 @@ static cudaError_t launch_persistent(stokes_batch b, int ty, int grid, int max_i
         return e;
     if ((e = cudaMemcpyAsync(b->d_st, b->d_st0, b->n * sizeof(BState), cudaMemcpyDeviceToDevice, b->s)) != cudaSuccess)
         return e;
-    size_t nw = std::max(1, b->nwork);
+    const size_t nw = b->wl_cap;
     const int* wi = b->d_wl;
     const int* wc = b->d_wl + nw;
     const int* wr = b->d_wl + 2 * nw;
@@ -821,13 +834,16 @@ stokes_status stokes_batch_solve(stokes_batch b, const stokes_batch_io* io, stok
     }
     cudaError_t e = cudaSuccess;
     if (b->sw) {
-        // the contexts' Schwarz plans are rebuilt after every weight build:
-        // refresh the instance table and patch list when any plan moved
+        // the contexts' Schwarz plans are rebuilt (all their buffers
+        // reallocated) after every weight build: refresh the instance table
+        // and patch list when any plan was rebuilt since the last upload.
+        // (Comparing one buffer's address is not enough: the allocator may
+        // hand that one back at the same address and move the others.)
         bool moved = false;
         for (int i = 0; i < b->n; ++i) {
             const SchwarzPlan* P = nullptr;
             if ((e = schwarz_ensure(b->c[i], &P)) != cudaSuccess) return STOKES_ERR_CUDA;
-            moved |= (int)b->plan_key.size() != b->n || P->fac != b->plan_key[i];
+            moved |= (int)b->plan_epoch.size() != b->n || b->c[i]->sw_epoch != b->plan_epoch[i];
         }
         if (moved && (e = upload_plan(b, b->ty)) != cudaSuccess) return STOKES_ERR_CUDA;
     }

@@ -86,6 +86,7 @@ struct Ctx {
     struct SchwarzPlan* sw = nullptr;
     std::vector<void*> sw_allocs;
     bool sw_ready = false;
+    unsigned sw_epoch = 0;       // incremented by every plan build (its buffers are reallocated)
     double sw_setup_ms = 0.0;
     // transport step (advect.cu): staged velocity and validity, allocated on first use
     void* adv_scratch = nullptr;

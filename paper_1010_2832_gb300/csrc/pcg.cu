@@ -262,6 +262,7 @@ static cudaError_t schwarz_build(Ctx* c) {
     cudaError_t e;
     for (void* p : c->sw_allocs) cudaFree(p);
     c->sw_allocs.clear();
+    ++c->sw_epoch;
     if (!c->sw) c->sw = new SchwarzPlan();
     SchwarzPlan& P = *c->sw;
     P.npx = (L.nx + 1 + PB - 1) / PB;
@@ -288,8 +289,8 @@ static cudaError_t schwarz_build(Ctx* c) {
     if ((e = al((void**)&P.corner, sizeof(int) * np)) != cudaSuccess) return e;
     if ((e = al((void**)&P.nloc, sizeof(int) * np)) != cudaSuccess) return e;
     if ((e = al((void**)&P.lmap, sizeof(short) * np * PMAX)) != cudaSuccess) return e;
-    // FP32 factors: BF16 storage halves the local-solve traffic but, measured
-    // on the 1024^2 bump workload, needs 4.4x the CG iterations
+    // FP16 factors with a FP32 scale per row (BF16 storage needed 4.4x the CG
+    // iterations on the 1024^2 bump workload; FP16 about 1.02x)
     if ((e = al((void**)&P.fac, (size_t)SW_FAC_BYTES * np)) != cudaSuccess) return e;
     if ((e = al((void**)&P.scale, sizeof(float) * np * PMAX)) != cudaSuccess) return e;
     if ((e = al((void**)&P.ybuf, sizeof(float) * ng * PMAX)) != cudaSuccess) return e;

@@ -126,3 +126,33 @@ def test_batched_schwarz_matches_oracle_and_beats_jacobi(tmp_path):
     assert [s["status"] for s in stats2] == [0] * len(wls)
     for a, c in zip(first, again):
         assert np.array_equal(a, c)
+
+
+def test_batched_recaptures_after_the_work_list_changes(tmp_path):
+    """Rebuilding one instance's weights from a different liquid shape (the
+    whole box full of liquid) changes the batch's work tiles and patch list
+    between two launches of its captured graph; the second solve must run on
+    the new lists: its result matches the oracle for the new shape, and the
+    untouched instance's result is unchanged."""
+    require_gpu()
+    from paper_1010_2832_gb300 import stokes
+    wls = [W.bumps_2d(n, seed=140 + i, rho_split=False, disk_r=0.05 + 0.02 * i) for i, n in enumerate([24, 40])]
+    b, ctxs, devs, outs, stats, ms = _batch(wls, 1e-11, tmp_path, precond=2)
+    assert [s["status"] for s in stats] == [0, 0], stats
+    kept = torch.cat([a.reshape(-1) for a in outs[1][0]]).cpu().numpy()
+    new = W.full_box(24, 2, seed=3)
+    d0 = stokes.upload_workload(new)
+    ctxs[0].build_weights(d0["phi_liquid"], d0["phi_solid"], d0["rho"], d0["mu"], d0["u_bc"])
+    ctxs[1].build_weights(devs[1]["phi_liquid"], devs[1]["phi_solid"], devs[1]["rho"], devs[1]["mu"],
+                          devs[1]["u_bc"])
+    for rep in range(2):                     # the second launch replays the new capture
+        stats2, _ = b.solve([d0["u_star"], devs[1]["u_star"]], [o[0] for o in outs], [o[1] for o in outs],
+                            [o[2] for o in outs])
+        assert [s["status"] for s in stats2] == [0, 0], stats2
+        S = oracle_system(new)
+        x_ref = So.solve_direct(S.A, S.b, S_.pressure_null_vectors(S))
+        u_ref = S_.recover_velocity(S, x_ref)
+        ug = torch.cat([a.reshape(-1) for a in outs[0][0]]).cpu().numpy()
+        lv = S.live
+        assert np.abs(ug - u_ref)[lv].max() <= 1e-8 * np.abs(u_ref[lv]).max()
+        assert np.array_equal(torch.cat([a.reshape(-1) for a in outs[1][0]]).cpu().numpy(), kept)
