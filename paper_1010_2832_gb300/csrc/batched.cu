@@ -231,13 +231,18 @@ __device__ __forceinline__ double batched_gather(const BInst& I, int f, int i, i
     const SchwarzPlan& P = I.sw;
     const int ilo = max((i + PB - 1) / PB - 1, 0), ihi = min((i + 1) / PB, P.npx - 1);
     const int jlo = max((j + PB - 1) / PB - 1, 0), jhi = min((j + 1) / PB, P.npy - 1);
-    float s = 0.f;
-    for (int J = jlo; J <= jhi; ++J)
-        for (int Ip = ilo; Ip <= ihi; ++Ip) {
-            const int ii = i - (PB * Ip - 1), jj = j - (PB * J - 1);
-            s += P.ybuf[(int64_t)(J * P.npx + Ip) * PMAX + (f * PR + jj) * PR + ii];
-        }
-    return (double)s;
+    // a fixed 2 x 2 window of patches, all loads issued before the sum (the
+    // ones outside the ranges masked, reading element 0)
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int Ip = ilo + (q & 1), J = jlo + (q >> 1);
+        const bool use = Ip <= ihi && J <= jhi;
+        const int ii = i - (PB * Ip - 1), jj = j - (PB * J - 1);
+        const float x = P.ybuf[use ? (int64_t)(J * P.npx + Ip) * PMAX + (f * PR + jj) * PR + ii : 0];
+        v[q] = use ? x : 0.f;
+    }
+    return (double)(((v[0] + v[1]) + v[2]) + v[3]);
 }
 
 template <int TY, bool SW>

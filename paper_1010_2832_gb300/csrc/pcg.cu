@@ -217,8 +217,11 @@ __global__ void __launch_bounds__(256) k_sw_init(Layout L, const int* __restrict
     }
 }
 
+// (at most 48 registers: five CTAs share an SM, each taking two tiles per
+// round, so up to 1,520 active tiles are one wave; the dots are float-float,
+// not FP64, whose arithmetic is slow on this part)
 template <int INIT>
-__global__ void __launch_bounds__(256) k_sw_finish(Layout L, const int* __restrict__ tiles, DevArrays D,
+__global__ void __launch_bounds__(256, 5) k_sw_finish(Layout L, const int* __restrict__ tiles, DevArrays D,
                                                    SchwarzPlan P, CgWork<float> w, CgScalars* sc, double* partial,
                                                    unsigned* counter, int ntiles, cudaGraphConditionalHandle h,
                                                    int use_cond) {
@@ -226,14 +229,25 @@ __global__ void __launch_bounds__(256) k_sw_finish(Layout L, const int* __restri
         if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
         return;
     }
-    double rz = 0.0, rr = 0.0;
-    // persistent over the tile list: one block reduction per CTA
-    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
-        const int tile = tiles[k];
-        const int c0 = (tile % L.ntx) * TX, r0 = (tile / L.ntx) * TY2;
-        schwarz_gather_slot(L, D, P, w.r, w.z, c0 + (threadIdx.x & 31), r0 + (threadIdx.x >> 5), rz, rr);
+    AccT<float> rz, rr;
+    // persistent over the tile list, two tiles per round (tile k and tile
+    // k + gridDim.x): the loads of both slots are issued before either is
+    // summed; one block reduction per CTA
+    for (int k = blockIdx.x; k < ntiles; k += 2 * gridDim.x) {
+        const int k2 = k + gridDim.x;
+        SwGather g0, g1;
+        const int t0 = tiles[k];
+        sw_gather_load(L, D, P, w.r, (t0 % L.ntx) * TX + (threadIdx.x & 31), (t0 / L.ntx) * TY2 + (threadIdx.x >> 5),
+                       g0);
+        if (k2 < ntiles) {
+            const int t1 = tiles[k2];
+            sw_gather_load(L, D, P, w.r, (t1 % L.ntx) * TX + (threadIdx.x & 31),
+                           (t1 / L.ntx) * TY2 + (threadIdx.x >> 5), g1);
+        }
+        sw_gather_finish(L, g0, w.z, rz, rr);
+        if (k2 < ntiles) sw_gather_finish(L, g1, w.z, rz, rr);
     }
-    block_partial2(warp_sum(rz), warp_sum(rr), partial, counter, gridDim.x, [&](double trz, double trr) {
+    block_partial2(rz.warp(), rr.warp(), partial, counter, gridDim.x, [&](double trz, double trr) {
         if (INIT) {
             const bool timed_out = sc->status == STOKES_ERR_TIMEOUT;   // set by a local solve
             sc->rz = trz; sc->rr = trr; sc->rr0 = trr;
@@ -349,7 +363,7 @@ static void schwarz_body(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, i
     launch_apply_mode<float, float>(L, c->tiles, nb, c->coef<float>(), w.z, w.q, MODE_CG, a, s);
     k_cg_xr<<<persist_grid((const void*)k_cg_xr, nb), 256, 0, s>>>(L, c->tiles, nb, c->nf, w, w.p[parity ^ 1], c->sc);
     launch_schwarz_gemv(L, *c->sw, w.r, c->sc, s);
-    k_sw_finish<0><<<persist_grid((const void*)k_sw_finish<0>, nb), 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc,
+    k_sw_finish<0><<<persist_grid((const void*)k_sw_finish<0>, (nb + 1) / 2), 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc,
                                                                                c->partial, c->counter, nb, h, use_cond);
 }
 
@@ -359,7 +373,7 @@ static void schwarz_start(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, 
     CgWork<float>& w = c->w32;
     k_sw_init<<<nb, 256, 0, s>>>(L, c->tiles, c->w64.r, w, c->sc);
     launch_schwarz_gemv(L, *c->sw, w.r, c->sc, s);
-    k_sw_finish<1><<<persist_grid((const void*)k_sw_finish<1>, nb), 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc,
+    k_sw_finish<1><<<persist_grid((const void*)k_sw_finish<1>, (nb + 1) / 2), 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc,
                                                                                c->partial, c->counter, nb, h, use_cond);
 }
 
@@ -717,7 +731,7 @@ cudaError_t apply_preconditioner(Ctx* c, int which, const float* r, float* z) {
     const int nb = c->ntiles_active;
     launch_schwarz_gemv(L, *c->sw, r, c->sc, s);
     if (nb)
-        k_sw_finish<1><<<persist_grid((const void*)k_sw_finish<1>, nb), 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc,
+        k_sw_finish<1><<<persist_grid((const void*)k_sw_finish<1>, (nb + 1) / 2), 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc,
                                                                                    c->partial, c->counter, nb, 0, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = fetch_scalars(c)) != cudaSuccess) return e;
@@ -820,7 +834,7 @@ cudaError_t apply_schwarz_noalloc(Ctx* c, const float* r, float* z, std::string*
     const int nb = c->ntiles_active;
     launch_schwarz_gemv(L, P, r, sc, s);
     if (nb)
-        k_sw_finish<1><<<persist_grid((const void*)k_sw_finish<1>, nb), 256, 0, s>>>(L, c->tiles, c->A, P, w, sc, partial,
+        k_sw_finish<1><<<persist_grid((const void*)k_sw_finish<1>, (nb + 1) / 2), 256, 0, s>>>(L, c->tiles, c->A, P, w, sc, partial,
                                                                                    counter, nb, 0, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     int status = 0;
@@ -901,7 +915,7 @@ cudaError_t bench_schwarz_kernels(Ctx* c, int launches, double* ms_local, double
     const int nb = c->ntiles_active;
     k_sw_init<<<nb, 256, 0, s>>>(L, c->tiles, c->b64, w, c->sc);
     launch_schwarz_gemv(L, P, w.r, c->sc, s);
-    k_sw_finish<1><<<persist_grid((const void*)k_sw_finish<1>, nb), 256, 0, s>>>(L, c->tiles, c->A, P, w, c->sc,
+    k_sw_finish<1><<<persist_grid((const void*)k_sw_finish<1>, (nb + 1) / 2), 256, 0, s>>>(L, c->tiles, c->A, P, w, c->sc,
                                                                                c->partial, c->counter, nb, 0, 0);
     std::vector<cudaEvent_t> ev(2 * launches + 1);
     for (auto& x : ev) cudaEventCreate(&x);
@@ -909,7 +923,7 @@ cudaError_t bench_schwarz_kernels(Ctx* c, int launches, double* ms_local, double
     for (int k = 0; k < launches; ++k) {
         launch_schwarz_gemv(L, P, w.r, c->sc, s);
         cudaEventRecord(ev[2 * k + 1], s);
-        k_sw_finish<0><<<persist_grid((const void*)k_sw_finish<0>, nb), 256, 0, s>>>(L, c->tiles, c->A, P, w, c->sc,
+        k_sw_finish<0><<<persist_grid((const void*)k_sw_finish<0>, (nb + 1) / 2), 256, 0, s>>>(L, c->tiles, c->A, P, w, c->sc,
                                                                                    c->partial, c->counter, nb, 0, 0);
         cudaEventRecord(ev[2 * k + 2], s);
     }

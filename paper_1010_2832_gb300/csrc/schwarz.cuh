@@ -371,38 +371,61 @@ static inline void launch_schwarz_gemv(const Layout& L, const SchwarzPlan& P, co
     if (P.np) k_schwarz_gemv<<<P.np, 128, SW_GEMV_SMEM, s>>>(L, P, r, sc);
 }
 
-__device__ __forceinline__ void schwarz_gather_slot(const Layout& L, const DevArrays& D, const SchwarzPlan& P,
-                                                    const float* __restrict__ r, float* __restrict__ z, int c,
-                                                    int rr, double& rz, double& r2) {
+// z at one slot (c, rr) from the patches' local results, in two parts so
+// that a thread can issue the loads of several slots before using any:
+// sw_gather_load issues every load (the residual, the activity flags and a
+// fixed 2 x 2 window of patches' results), sw_gather_finish sums, writes z
+// and accumulates r.z and r.r.  Inactive unknowns take z = r (zero outside
+// the grid).
+struct SwGather {
+    float rv[3], v[3][4];
+    bool act[3], use[4], real;
+    int64_t o;
+};
+
+__device__ __forceinline__ void sw_gather_load(const Layout& L, const DevArrays& D, const SchwarzPlan& P,
+                                               const float* __restrict__ r, int c, int rr, SwGather& g) {
     const int i = c - 1, j = rr - 1;
-    const int64_t o = L.off(c, rr, 0);
+    g.o = L.off(c, rr, 0);
     // patch I's ring covers slots [PB I - 1, PB I + PB]:
     // I from ceil(i / PB) - 1 to floor((i + 1) / PB)   (i >= 0)
     const int ilo = max((i + PB - 1) / PB - 1, 0), ihi = min((i + 1) / PB, P.npx - 1);
     const int jlo = max((j + PB - 1) / PB - 1, 0), jhi = min((j + 1) / PB, P.npy - 1);
-    const bool real = i >= 0 && j >= 0 && i <= L.nx && j <= L.ny;
-    // every load is independent: the local results are zero for inactive
-    // patches and for inactive unknowns, so they are summed unconditionally
-    float rv[3], sum[3];
-    bool act[3];
+    g.real = i >= 0 && j >= 0 && i <= L.nx && j <= L.ny;
+    // a fixed 2 x 2 window of patches (ilo.., jlo..); the ones outside
+    // [ilo, ihi] x [jlo, jhi] (which may lie past the patch grid) are masked
+    // and read element 0 instead.  Inside the ranges the ring position is in
+    // [0, PR) (PB I - 1 <= i <= PB I + PB).  The local results are zero for
+    // inactive patches and unknowns, so they are summed unconditionally.
+    // (The results hold npy npx PMAX floats, far below 2^31.)
+    int base[4];
 #pragma unroll
-    for (int f = 0; f < 3; ++f) {
-        rv[f] = r[(int64_t)f * L.stride + o];
-        act[f] = unknown_active(D, L, f, i, j);
-        float s = 0.f;
-        for (int J = jlo; J <= jhi; ++J)
-            for (int I = ilo; I <= ihi; ++I) {
-                const int ii = i - (PB * I - 1), jj = j - (PB * J - 1);
-                s += P.ybuf[(int64_t)(J * P.npx + I) * PMAX + (f * PR + jj) * PR + ii];
-            }
-        sum[f] = s;
+    for (int q = 0; q < 4; ++q) {
+        const int I = ilo + (q & 1), J = jlo + (q >> 1);
+        g.use[q] = I <= ihi && J <= jhi;
+        const int ii = i - (PB * I - 1), jj = j - (PB * J - 1);
+        base[q] = g.use[q] ? (J * P.npx + I) * PMAX + jj * PR + ii : 0;
     }
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-        const float zv = act[f] ? sum[f] : (real ? rv[f] : 0.f);
-        z[(int64_t)f * L.stride + o] = zv;
-        rz += (double)rv[f] * zv;
-        r2 += (double)rv[f] * rv[f];
+        g.rv[f] = r[(int64_t)f * L.stride + g.o];
+        g.act[f] = unknown_active(D, L, f, i, j);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) g.v[f][q] = P.ybuf[g.use[q] ? base[q] + f * PR * PR : 0];
+    }
+}
+
+__device__ __forceinline__ void sw_gather_finish(const Layout& L, const SwGather& g, float* __restrict__ z,
+                                                 AccT<float>& rz, AccT<float>& r2) {
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        float s = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s += g.use[q] ? g.v[f][q] : 0.f;
+        const float zv = g.act[f] ? s : (g.real ? g.rv[f] : 0.f);
+        z[(int64_t)f * L.stride + g.o] = zv;
+        rz.add(g.rv[f], zv);          // float-float: FP64 arithmetic is slow on this part
+        r2.add(g.rv[f], g.rv[f]);
     }
 }
 
