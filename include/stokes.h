@@ -180,7 +180,8 @@ typedef struct {
                           (flexible CG, see stokes_set_learned_preconditioner);
                           2 = additive Schwarz, 2D: overlapping patches of
                           4x4 slots plus a one-slot ring, exact local solves
-                          (BF16-stored inverses, FP32 inner CG)               */
+                          (inverse factors stored in FP16 with a FP32 scale
+                          per row, FP32 inner CG)                             */
     int use_graph;     /* 1: CG loop in a device-side CUDA graph (conditional
                           while node); 0: host-driven chunks of check_every
                           iterations launched one kernel at a time (for
