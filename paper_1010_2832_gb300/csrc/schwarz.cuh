@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
 // products (sw_factor_products); rotate back and store by position.  A copy
 // that never completes (bounded wait) marks the solve STOKES_ERR_TIMEOUT and
 // ends it.
-__global__ void __launch_bounds__(128) k_schwarz_gemv(Layout L, SchwarzPlan P, const float* __restrict__ r,
+__global__ void __launch_bounds__(128, 15) k_schwarz_gemv(Layout L, SchwarzPlan P, const float* __restrict__ r,
                                                       CgScalars* sc) {
     extern __shared__ __align__(128) uint8_t Fs[];             // SW_FAC_BYTES
     __shared__ __align__(16) float s[PMAX8];
