@@ -50,8 +50,8 @@ __global__ void k_schwarz_mark(Layout L, DevArrays D, int npx, int npy, int* fla
 // face terms leaves some patch matrices indefinite.  Only the unit-diagonal
 // matrix is rounded to FP32 for the factorisation.  Every global load is
 // issued in parallel (activity flags, then the coefficients of the faces
-// touching the patch, staged in shared memory); one warp then accumulates
-// the faces in a fixed order, so the local matrices are reproducible bit for
+// touching the patch, staged in shared memory); each thread accumulates one
+// row, faces in a fixed order, so the local matrices are reproducible bit for
 // bit.  Dynamic smem: the FP64 matrix (PMAX^2 doubles), whose upper half
 // later holds the scaled FP32 matrix and whose lower half the inverse factor
 // X = L^-1, then the diagonal scaling: about 94 KB, two CTAs per SM.
@@ -137,28 +137,29 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
         }
         fK[t] = K;
     }
-    // 3. stress diagonal C
-    for (int e = t; e < 2 * PR * PR; e += 256) {
-        int f = e / (PR * PR), rem = e % (PR * PR), jj = rem / PR, ii = rem % PR;
-        int k = map[(f * PR + jj) * PR + ii];
-        if (k >= 0) {
-            int64_t o = L.off(a0 + ii + 1, b0 + jj + 1, 0);
-            Ad[k * PMAX + k] += (f == 0 ? d_c : d_n)[o];
-        }
-    }
     __syncthreads();
-    // 4. K_f beta_f beta_f^T of every face, one warp, faces in order; lanes own
-    // distinct (row, column) pairs of one face's 6x6 outer product
-    if (t < 32) {
-        for (int f = 0; f < SW_NFACE; ++f) {
-            const double K = fK[f];
+    // 3. row r of A_p by thread r: the stress diagonal C, then K_f b_f b_f^T
+    // of every face containing r, faces in order (each entry sums the same
+    // terms in the same order whichever thread owns it: reproducible bit for
+    // bit)
+    if (t < n) {
+        double* row = Ad + (int64_t)t * PMAX;
+        int pos = -1;                     // position (field, ring row, ring column) of unknown t
+        for (int e = 0; e < PMAX; ++e)
+            if (map[e] == t) { pos = e; break; }
+        const int f = pos / (PR * PR), cell = pos % (PR * PR);
+        if (f < 2) row[t] += (f == 0 ? d_c : d_n)[L.off(a0 + cell % PR + 1, b0 + cell / PR + 1, 0)];
+        for (int fc = 0; fc < SW_NFACE; ++fc) {
+            const double K = fK[fc];
             if (K == 0.0) continue;
-            for (int q = t; q < 36; q += 32) {
-                const int r = q / 6, c = q % 6;
-                const int ir = fidx[f][r], ic = fidx[f][c];
-                if (ir >= 0 && ic >= 0) Ad[ir * PMAX + ic] += K * fb[f][r] * fb[f][c];
+            for (int q = 0; q < 6; ++q) {
+                if (fidx[fc][q] != t) continue;
+                const double kb = K * fb[fc][q];
+                for (int c = 0; c < 6; ++c) {
+                    const int ic = fidx[fc][c];
+                    if (ic >= 0) row[ic] += kb * fb[fc][c];
+                }
             }
-            __syncwarp();
         }
     }
     __syncthreads();
@@ -213,39 +214,48 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
         }
         __syncthreads();
     }
-    // 7. Cholesky (lower, in place, FP32)
+    // 7. Cholesky (lower, in place, FP32).  Column k is copied to colk once
+    // scaled; the trailing update runs on a 16 x 16 thread grid (thread
+    // (tr, tc): rows k+1+tr+16i, columns k+1+tc+16j <= row), lower triangle only
+    __shared__ float colk[PMAX];
+    const int tr = t >> 4, tc = t & 15;
     for (int k = 0; k < n; ++k) {
         if (t == 0) {
             float d = A[k * PMAX + k];
             A[k * PMAX + k] = d > 1e-12f ? sqrtf(d) : 1.f;    // a vanishing pivot is replaced (robust, still SPD)
         }
         __syncthreads();
-        float piv = A[k * PMAX + k];
-        for (int r = k + 1 + t; r < n; r += 256) A[r * PMAX + k] /= piv;
+        const float piv = A[k * PMAX + k];
+        for (int r = k + 1 + t; r < n; r += 256) {
+            const float v = A[r * PMAX + k] / piv;
+            A[r * PMAX + k] = v;
+            colk[r] = v;
+        }
         __syncthreads();
-        int m = n - k - 1;
-        for (int e = t; e < m * m; e += 256) {
-            int r = k + 1 + e / m, c = k + 1 + e % m;
-            if (c <= r) A[r * PMAX + c] -= A[r * PMAX + k] * A[c * PMAX + k];
+        for (int r = k + 1 + tr; r < n; r += 16) {
+            const float lr = colk[r];
+            float* Ar = A + r * PMAX;
+            for (int c = k + 1 + tc; c <= r; c += 16) Ar[c] -= lr * colk[c];
         }
         __syncthreads();
     }
     // 8. X = L^-1 by forward elimination on the identity, all columns at
     // once: row k is final once divided by L_kk, then eliminated from the
-    // rows below (every step parallel over the rows and columns it touches)
-    for (int e = t; e < n * n; e += 256) {
-        const int r = e / n, c = e % n;
-        X[r * PMAX + c] = r == c ? 1.f : 0.f;
+    // rows below (thread (tr, tc): rows k+1+tr+16i, columns tc+16j <= k)
+    for (int e = t; e < n * PMAX; e += 256) {
+        const int r = e / PMAX, c = e - r * PMAX;
+        if (c < n) X[e] = r == c ? 1.f : 0.f;
     }
     __syncthreads();
     for (int k = 0; k < n; ++k) {
         const float inv = 1.f / A[k * PMAX + k];
         for (int c = t; c <= k; c += 256) X[k * PMAX + c] *= inv;
         __syncthreads();
-        const int m = n - k - 1;
-        for (int e = t; e < m * (k + 1); e += 256) {
-            const int r = k + 1 + e / (k + 1), c = e % (k + 1);
-            X[r * PMAX + c] -= A[r * PMAX + k] * X[k * PMAX + c];
+        const float* Xk = X + k * PMAX;
+        for (int r = k + 1 + tr; r < n; r += 16) {
+            const float lr = A[r * PMAX + k];
+            float* Xr = X + r * PMAX;
+            for (int c = tc; c <= k; c += 16) Xr[c] -= lr * Xk[c];
         }
         __syncthreads();
     }
