@@ -76,15 +76,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 }
 
 // Start the bulk (TMA) copy of one packed factor into shared memory,
-// completing on mbarrier `bar` (one thread).
+// completing on mbarrier `bar` (one thread).  The factors are read once per
+// CG iteration and are larger than L2: they are loaded with an evict-first
+// L2 policy, so that the solver's vectors and coefficients stay in L2.
 __device__ __forceinline__ void sw_issue(uint32_t bar, void* dst, const void* src, uint32_t bytes) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    if (bytes > 0)
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                         smem_u32(dst)),
-                     "l"(src), "r"(bytes), "r"(bar)
-                     : "memory");
+    if (bytes > 0) {
+        uint64_t pol;
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+            "%4;" ::"r"(smem_u32(dst)),
+            "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+            : "memory");
+    }
 }
 
 // s <- X~^T diag(rho^2) X~ s for the stored factor F of an n-unknown patch in
