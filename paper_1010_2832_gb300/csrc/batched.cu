@@ -157,7 +157,7 @@ __device__ void batched_local_solve(const BInst& I, int p, double alpha, uint8_t
     if (!ok_s) return;
     const int n = P.nloc[p];
     const uint32_t b_addr = smem_u32(bar);
-    if (t == 0) sw_issue(b_addr, Fs, P.fac + (int64_t)p * SW_FAC_BYTES, sw_patch_bytes(n));
+    if (t == 0) sw_issue(b_addr, Fs, P.fac + (int64_t)p * SW_FAC_BYTES, sw_patch_bytes(n), P.evict_first != 0);
     constexpr float H = 0.70710678118654752f;
     const int CI = P.corner[p] & 0xffff, CJ = P.corner[p] >> 16;
     const int a0 = PB * CI - 1, b0 = PB * CJ - 1;
@@ -231,18 +231,16 @@ __device__ __forceinline__ double batched_gather(const BInst& I, int f, int i, i
     const SchwarzPlan& P = I.sw;
     const int ilo = max((i + PB - 1) / PB - 1, 0), ihi = min((i + 1) / PB, P.npx - 1);
     const int jlo = max((j + PB - 1) / PB - 1, 0), jhi = min((j + 1) / PB, P.npy - 1);
-    // a fixed 2 x 2 window of patches, all loads issued before the sum (the
-    // ones outside the ranges masked, reading element 0)
-    float v[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int Ip = ilo + (q & 1), J = jlo + (q >> 1);
-        const bool use = Ip <= ihi && J <= jhi;
-        const int ii = i - (PB * Ip - 1), jj = j - (PB * J - 1);
-        const float x = P.ybuf[use ? (int64_t)(J * P.npx + Ip) * PMAX + (f * PR + jj) * PR + ii : 0];
-        v[q] = use ? x : 0.f;
-    }
-    return (double)(((v[0] + v[1]) + v[2]) + v[3]);
+    // (a loop over the patches in range: a fixed, masked 2 x 2 window as in
+    // the single-system gather needs more registers here, which costs this
+    // persistent kernel a CTA per SM)
+    float s = 0.f;
+    for (int J = jlo; J <= jhi; ++J)
+        for (int Ip = ilo; Ip <= ihi; ++Ip) {
+            const int ii = i - (PB * Ip - 1), jj = j - (PB * J - 1);
+            s += P.ybuf[(int64_t)(J * P.npx + Ip) * PMAX + (f * PR + jj) * PR + ii];
+        }
+    return (double)s;
 }
 
 template <int TY, bool SW>
@@ -543,6 +541,14 @@ static cudaError_t upload_plan(stokes_batch b, int ty) {
     std::vector<BInst> insts;
     cudaError_t e = build_worklist(b, ty, wi, wc, wr, insts);
     if (e != cudaSuccess) return e;
+    if (b->sw) {
+        // the batch's factors stream through L2 together: the evict-first
+        // policy applies when all of them together exceed half of L2
+        size_t tot = 0;
+        for (const BInst& I : insts) tot += (size_t)I.sw.np * SW_FAC_BYTES;
+        const int ef = sw_factors_exceed_l2(tot) ? 1 : 0;
+        for (BInst& I : insts) I.sw.evict_first = ef;
+    }
     const int old_nwork = b->nwork;
     b->nwork = (int)wi.size();
     std::vector<BState> st0(b->n);

@@ -298,6 +298,7 @@ static cudaError_t schwarz_build(Ctx* c) {
         for (int I = 0; I < P.npx; ++I)
             if (flag[J * P.npx + I]) { pid[J * P.npx + I] = (int)corner.size(); corner.push_back(I | (J << 16)); }
     P.np = (int)corner.size();
+    P.evict_first = sw_factors_exceed_l2((size_t)P.np * SW_FAC_BYTES) ? 1 : 0;
     const size_t np = std::max(1, P.np);
     if ((e = al((void**)&P.pid, sizeof(int) * ng)) != cudaSuccess) return e;
     if ((e = al((void**)&P.corner, sizeof(int) * np)) != cudaSuccess) return e;

@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(128, 15) k_schwarz_gemv(Layout L, SchwarzPlan 
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_addr), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        sw_issue(b_addr, Fs, P.fac + (int64_t)p * SW_FAC_BYTES, sw_patch_bytes(n));
+        sw_issue(b_addr, Fs, P.fac + (int64_t)p * SW_FAC_BYTES, sw_patch_bytes(n), P.evict_first != 0);
     }
     constexpr float H = 0.70710678118654752f;
     const int I = P.corner[p] & 0xffff, J = P.corner[p] >> 16;

@@ -37,6 +37,8 @@ struct SchwarzPlan {
     float* ybuf;                    // [npy * npx * PMAX] local results by grid patch and position
                                     // (f, jj, ii); zero for inactive patches and positions
     int np;
+    int evict_first;                // the factors (of this plan, or of a whole batch) exceed half of
+                                    // L2: load them with an evict-first L2 policy
 };
 
 // Whether the unknown of field f (0 tau_xx at a cell, 1 tau_xy at a node,
@@ -77,12 +79,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 // Start the bulk (TMA) copy of one packed factor into shared memory,
 // completing on mbarrier `bar` (one thread).  The factors are read once per
-// CG iteration and are larger than L2: they are loaded with an evict-first
-// L2 policy, so that the solver's vectors and coefficients stay in L2.
-__device__ __forceinline__ void sw_issue(uint32_t bar, void* dst, const void* src, uint32_t bytes) {
+// CG iteration; when they do not fit in L2 (evict_first) they are loaded
+// with an evict-first L2 policy, so that the solver's vectors and
+// coefficients stay in L2 instead of being evicted by the stream; when they
+// fit, the default policy keeps them resident from one iteration to the next.
+__device__ __forceinline__ void sw_issue(uint32_t bar, void* dst, const void* src, uint32_t bytes,
+                                         bool evict_first) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    if (bytes > 0) {
+    if (bytes == 0) return;
+    if (evict_first) {
         uint64_t pol;
         asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
         asm volatile(
@@ -90,7 +96,20 @@ __device__ __forceinline__ void sw_issue(uint32_t bar, void* dst, const void* sr
             "%4;" ::"r"(smem_u32(dst)),
             "l"(src), "r"(bytes), "r"(bar), "l"(pol)
             : "memory");
+    } else {
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(dst)),
+                     "l"(src), "r"(bytes), "r"(bar)
+                     : "memory");
     }
+}
+
+// Whether factor bytes exceed half of this device's L2 (host).
+inline bool sw_factors_exceed_l2(size_t bytes) {
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    return l2 > 0 && bytes > (size_t)l2 / 2;
 }
 
 // s <- X~^T diag(rho^2) X~ s for the stored factor F of an n-unknown patch in
