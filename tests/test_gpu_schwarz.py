@@ -3,9 +3,8 @@ in the oracle (dense FP64 local solves), and solves with it.
 
 The GPU assembles each local matrix in FP64, factors the unit-diagonal
 matrix in FP32, stores the inverse X = L^-1 of the factor in FP16 with a
-FP32 factor per row and applies D^-1/2 X^T X D^-1/2 with FP32
-accumulation, so the preconditioned
-vector agrees with the FP64 definition to about 1e-2 relative (RMS; the
+FP32 scale per row and applies D^-1/2 X^T X D^-1/2 with FP32
+accumulation, so the preconditioned vector agrees with the FP64 definition to about 1e-2 relative (RMS; the
 error concentrates in the worst-conditioned patches) while the
 preconditioner stays symmetric positive definite (checked on random
 vectors).  The solve is judged by the FP64 true residual; it must stay in
