@@ -390,9 +390,11 @@ static cudaError_t launch_mode(const Layout& L, const int* tiles, int ntiles, co
     static int cache2[16], cache3[16];
     if (L.dim == 2) {
         // FP32 vectors: at most 64 registers, four CTAs per SM (measured 70% of
-        // HBM at 4096^2, against 54% with 96 registers and three CTAs); FP64
-        // is bound by the FP64 pipe, where the unconstrained build is faster
-        constexpr int MINB = sizeof(T) == 4 ? 4 : 1;
+        // HBM at 4096^2, against 54% with 96 registers and three CTAs, 67% with
+        // five); BF16 coefficients: five CTAs per SM (44% against 38% with
+        // four); FP64 is bound by the FP64 pipe, where the unconstrained build
+        // is faster
+        constexpr int MINB = sizeof(C) == 2 ? 5 : (sizeof(T) == 4 ? 4 : 1);
         const int grid = std::min(ntiles, resident_ctas((const void*)k_apply2d<T, C, MODE, MINB>, 256, 0, cache2));
         k_apply2d<T, C, MODE, MINB><<<grid, 256, 0, s>>>(L, tiles, cf, x, y, a, ntiles);
     } else {
