@@ -231,15 +231,19 @@ __global__ void __launch_bounds__(256, MINB) k_apply2d(Layout L, const int* __re
 //   y_txy = d_xy txy + a_xy [z_u(r) - z_u(r-1) + z_v(c) - z_v(c-1)]
 //   y_txz = d_xz txz + a_xz [z_u(q) - z_u(q-1) + z_w(c) - z_w(c-1)]
 //   y_tyz = d_yz tyz + a_yz [z_v(q) - z_v(q-1) + z_w(r) - z_w(r-1)]
+// Staged values; the face values z_u, z_v, z_w are written over U, V, W once
+// every face has been formed (held in registers meanwhile), which keeps the
+// shared memory at six staged arrays (6 CTAs per SM for FP32 instead of 5).
 template <class T> struct Smem3 {
     static constexpr int SX = TX + 2, SY = TY3 + 2, SZ = TZ3 + 2, NS = SX * SY * SZ;
     static constexpr int ZX = TX + 1, ZY = TY3 + 1, ZZ = TZ3 + 1, NZ = ZX * ZY * ZZ;
+    static constexpr int ZPT = (NZ + 255) / 256;      // face positions per thread
+    static_assert(NZ <= NS, "faces are stored over the staged arrays");
     T U[NS], V[NS], W[NS], Nxy[NS], Nxz[NS], Nyz[NS];
-    T zu[NZ], zv[NZ], zw[NZ];
 };
 
 template <class T, class C, int MODE>
-__global__ void __launch_bounds__(256) k_apply3d(Layout L, const int* __restrict__ tiles, Coef<C> cf,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) k_apply3d(Layout L, const int* __restrict__ tiles, Coef<C> cf,
                                                  const T* __restrict__ x, T* __restrict__ y, ApplyArgs args,
                                                  int ntiles) {
     using SM = Smem3<T>;
@@ -282,29 +286,45 @@ __global__ void __launch_bounds__(256) k_apply3d(Layout L, const int* __restrict
     __syncthreads();
     // staged index of (c, r, q) relative to (c0-1, r0-1, q0-1)
     auto si = [](int ii, int jj, int kk) { return (kk * SM::SY + jj) * SM::SX + ii; };
-    for (int e = t; e < SM::NZ; e += 256) {
+    T fzu[SM::ZPT], fzv[SM::ZPT], fzw[SM::ZPT];
+#pragma unroll
+    for (int it = 0; it < SM::ZPT; ++it) {
+        const int e = t + 256 * it;
+        if (e >= SM::NZ) break;
         int ii = e % SM::ZX, rest = e / SM::ZX, jj = rest % SM::ZY, kk = rest / SM::ZY;
         // z_u at (c0+ii, r0-1+jj, q0-1+kk): staged coords (ii+1, jj, kk)
         {
             int s = si(ii + 1, jj, kk);
             T ku = ld<T, C>(K_u, L.off(c0 + ii, r0 - 1 + jj, q0 - 1 + kk));
-            sm.zu[e] = ku * ((sm.U[s] - sm.U[s - 1]) + (sm.Nxy[s] - sm.Nxy[s + SM::SX]) +
-                             (sm.Nxz[s] - sm.Nxz[s + SM::SX * SM::SY]));
+            fzu[it] = ku * ((sm.U[s] - sm.U[s - 1]) + (sm.Nxy[s] - sm.Nxy[s + SM::SX]) +
+                            (sm.Nxz[s] - sm.Nxz[s + SM::SX * SM::SY]));
         }
         // z_v at (c0-1+ii, r0+jj, q0-1+kk): staged (ii, jj+1, kk)
         {
             int s = si(ii, jj + 1, kk);
             T kv = ld<T, C>(K_v, L.off(c0 - 1 + ii, r0 + jj, q0 - 1 + kk));
-            sm.zv[e] = kv * ((sm.V[s] - sm.V[s - SM::SX]) + (sm.Nxy[s] - sm.Nxy[s + 1]) +
-                             (sm.Nyz[s] - sm.Nyz[s + SM::SX * SM::SY]));
+            fzv[it] = kv * ((sm.V[s] - sm.V[s - SM::SX]) + (sm.Nxy[s] - sm.Nxy[s + 1]) +
+                            (sm.Nyz[s] - sm.Nyz[s + SM::SX * SM::SY]));
         }
         // z_w at (c0-1+ii, r0-1+jj, q0+kk): staged (ii, jj, kk+1)
         {
             int s = si(ii, jj, kk + 1);
             T kw = ld<T, C>(K_w, L.off(c0 - 1 + ii, r0 - 1 + jj, q0 + kk));
-            sm.zw[e] = kw * ((sm.W[s] - sm.W[s - SM::SX * SM::SY]) + (sm.Nxz[s] - sm.Nxz[s + 1]) +
-                             (sm.Nyz[s] - sm.Nyz[s + SM::SX]));
+            fzw[it] = kw * ((sm.W[s] - sm.W[s - SM::SX * SM::SY]) + (sm.Nxz[s] - sm.Nxz[s + 1]) +
+                            (sm.Nyz[s] - sm.Nyz[s + SM::SX]));
         }
+    }
+    __syncthreads();                           // every staged value is read: faces go over U, V, W
+    T* const zua = sm.U;
+    T* const zva = sm.V;
+    T* const zwa = sm.W;
+#pragma unroll
+    for (int it = 0; it < SM::ZPT; ++it) {
+        const int e = t + 256 * it;
+        if (e >= SM::NZ) break;
+        zua[e] = fzu[it];
+        zva[e] = fzv[it];
+        zwa[e] = fzw[it];
     }
     __syncthreads();
     auto zi = [](int ii, int jj, int kk) { return (kk * SM::ZY + jj) * SM::ZX + ii; };
@@ -317,14 +337,14 @@ __global__ void __launch_bounds__(256) k_apply3d(Layout L, const int* __restrict
 #pragma unroll
         for (int f = 0; f < 6; ++f) v[f] = MODE == MODE_CG ? pnew[f * S + o] : x[f * S + o];
         // z_u(c, r, q): index (tx, ty+1, tz+1); z_u(c+1): (tx+1, ...)
-        T zu = sm.zu[zi(tx, ty + 1, tz + 1)], zu_cp = sm.zu[zi(tx + 1, ty + 1, tz + 1)];
-        T zu_rm = sm.zu[zi(tx, ty, tz + 1)], zu_qm = sm.zu[zi(tx, ty + 1, tz)];
+        T zu = zua[zi(tx, ty + 1, tz + 1)], zu_cp = zua[zi(tx + 1, ty + 1, tz + 1)];
+        T zu_rm = zua[zi(tx, ty, tz + 1)], zu_qm = zua[zi(tx, ty + 1, tz)];
         // z_v(c, r, q): (tx+1, ty, tz+1)
-        T zv = sm.zv[zi(tx + 1, ty, tz + 1)], zv_rp = sm.zv[zi(tx + 1, ty + 1, tz + 1)];
-        T zv_cm = sm.zv[zi(tx, ty, tz + 1)], zv_qm = sm.zv[zi(tx + 1, ty, tz)];
+        T zv = zva[zi(tx + 1, ty, tz + 1)], zv_rp = zva[zi(tx + 1, ty + 1, tz + 1)];
+        T zv_cm = zva[zi(tx, ty, tz + 1)], zv_qm = zva[zi(tx + 1, ty, tz)];
         // z_w(c, r, q): (tx+1, ty+1, tz)
-        T zw = sm.zw[zi(tx + 1, ty + 1, tz)], zw_qp = sm.zw[zi(tx + 1, ty + 1, tz + 1)];
-        T zw_cm = sm.zw[zi(tx, ty + 1, tz)], zw_rm = sm.zw[zi(tx + 1, ty, tz)];
+        T zw = zwa[zi(tx + 1, ty + 1, tz)], zw_qp = zwa[zi(tx + 1, ty + 1, tz + 1)];
+        T zw_cm = zwa[zi(tx, ty + 1, tz)], zw_rm = zwa[zi(tx + 1, ty, tz)];
         T ac = ld<T, C>(a_c, o), dc = ld<T, C>(d_c, o);
         T yv[6];
         if (ac != T(0)) {
