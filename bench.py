@@ -43,7 +43,6 @@ KERNEL_SOURCES = {
 # dram__bytes_write.sum per launch from one ncu capture of the same command)
 NCU_TRAFFIC = {
     ("bumps1024", "fp32", "k_schwarz_gemv"): ("79664602fe4c8660", 241.689344e6),   # profiles/k_schwarz_gemv_bumps1024.md
-    ("bumps1024", "fp32", "k_apply2d"): ("00443ece1ab7fc9c", 17.073536e6),          # profiles/k_apply2d_bumps1024.md
 }
 
 
