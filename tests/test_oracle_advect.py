@@ -76,3 +76,23 @@ def test_extension_spreads_a_constant_and_keeps_valid_values():
     assert np.all(g[filled] == 2.5)
     assert filled.sum() > valid.sum()
     assert np.array_equal(g[valid], f[valid])
+
+
+def test_extension_rule_on_hand_worked_cases():
+    """One sweep fills exactly the invalid samples with a valid 4-neighbour
+    (not diagonal ones) with the mean of those neighbours; a second sweep
+    continues from the first one's values."""
+    row = np.array([[1.0, np.nan, np.nan, np.nan, 5.0]])
+    ok = np.array([[True, False, False, False, True]])
+    one = Ad.extend(row, ok, 1)
+    assert one[0, 1] == 1.0 and one[0, 3] == 5.0 and np.isnan(one[0, 2])
+    two = Ad.extend(row, ok, 2)
+    assert two[0, 2] == 3.0                                   # mean of 1 and 5
+    sq = np.full((3, 3), np.nan)
+    sq[0, 0] = 2.0
+    okq = np.zeros((3, 3), bool)
+    okq[0, 0] = True
+    g = Ad.extend(sq, okq, 1)
+    assert g[0, 1] == 2.0 and g[1, 0] == 2.0 and np.isnan(g[1, 1])   # no diagonal neighbours
+    g2 = Ad.extend(sq, okq, 2)
+    assert g2[1, 1] == 2.0 and g2[0, 2] == 2.0 and np.isnan(g2[2, 2])
