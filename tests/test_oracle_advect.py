@@ -1,7 +1,10 @@
 """Pins of the fractional-step reference (oracle.advect): no motion is the
 identity, a uniform velocity transports a linear field exactly (bilinear
 interpolation reproduces it), a shift by whole cells moves samples onto
-their neighbours, gravity adds dt g, and the extension spreads a constant."""
+their neighbours, gravity adds dt g, shear flows are steady (each velocity
+component is advected by the full velocity), departures beyond the samples
+clamp onto the boundary, and the extension fills invalid samples with the
+mean of their valid 4-neighbours, one ring per sweep."""
 import numpy as np
 
 from oracle import advect as Ad
@@ -96,3 +99,27 @@ def test_extension_rule_on_hand_worked_cases():
     assert g[0, 1] == 2.0 and g[1, 0] == 2.0 and np.isnan(g[1, 1])   # no diagonal neighbours
     g2 = Ad.extend(sq, okq, 2)
     assert g2[1, 1] == 2.0 and g2[0, 2] == 2.0 and np.isnan(g2[2, 2])
+
+
+def test_shear_flows_are_steady_and_far_departures_clamp():
+    """u = y (v = 0) and v = x (u = 0) are steady under pure advection: each
+    component is constant along its own streamlines, so both must come back
+    unchanged (a swapped component would move them); a level set that
+    depends only on the coordinate the flow does not change is unchanged.
+    A departure point far outside the lattice takes the boundary sample."""
+    dt = 0.07
+    u, v = _faces(lambda x, y: y, lambda x, y: 0.0 * x)
+    us, vs = Ad.advect_velocity(u, v, H, dt, (0.0, 0.0))
+    assert np.abs(us - u).max() <= 1e-14 and np.abs(vs).max() == 0.0
+    phi = _lattice(lambda x, y: 0.2 + y)
+    assert np.abs(Ad.advect_levelset(phi, u, v, H, dt) - phi).max() <= 1e-14
+    u2, v2 = _faces(lambda x, y: 0.0 * x, lambda x, y: x)
+    us2, vs2 = Ad.advect_velocity(u2, v2, H, dt, (0.0, 0.0))
+    assert np.abs(vs2 - v2).max() <= 1e-14 and np.abs(us2).max() == 0.0
+    # far departures: every lattice point's departure lies left of the lattice
+    big = 1e3
+    ub, vb = _faces(lambda x, y: big + 0 * x, lambda x, y: 0.0 * x)
+    rng = np.random.default_rng(5)
+    phi = rng.normal(size=(2 * N[1] + 3, 2 * N[0] + 3))
+    new = Ad.advect_levelset(phi, ub, vb, H, 1.0)
+    assert np.array_equal(new, np.repeat(phi[:, :1], phi.shape[1], axis=1))
