@@ -22,10 +22,22 @@ def relative_residual(A, x, b):
 
 
 def solve_direct(A, b, null_vectors=()):
-    """Sparse LU solve.  Each null vector (enclosed-liquid pressure mode,
-    Section 8) is removed by fixing one of its entries to zero, as the paper
-    suggests; the returned x is one solution of the consistent system."""
+    """Sparse LU solve.  Each null vector v (enclosed-liquid pressure mode,
+    Section 8, last paragraph: pressures that differ by a constant give the
+    same velocities) is handled in two steps.  First the component of b
+    along v is removed: a prescribed wall velocity whose discrete flux out of
+    the enclosed region is not exactly zero (any non-rigid u_BC; the defect
+    is a discretization error) makes A x = b inconsistent, and then fixing a
+    pressure would put the whole defect into the equation of the pinned cell
+    (a point source of mass there).  Then one entry of v is fixed to zero, as
+    the paper suggests.  For consistent data the first step changes b only
+    by rounding; the result is the solution that conjugate gradients
+    converges to, up to the null component of x, which does not change the
+    velocities."""
     n = A.shape[0]
+    b = np.asarray(b, dtype=np.float64).copy()
+    for v in null_vectors:
+        b -= (v @ b) / (v @ v) * v
     pin = [int(np.flatnonzero(v)[0]) for v in null_vectors]
     keep = np.setdiff1d(np.arange(n), pin)
     Ak = A.tocsc()[keep][:, keep]
