@@ -439,10 +439,12 @@ double stokes_schwarz_setup_ms(stokes_ctx ctx);
  * 540^2 (larger grids: STOKES_ERR_ARG with the sizes in stokes_last_error).
  * The context's Schwarz plan must already exist (an earlier
  * stokes_apply_preconditioner(ctx, 2, ...) or a solve with precond = 2 after
- * the last weight build), else STOKES_ERR_STATE.  The array's address is
- * looked up on the first call on each device, with that device current: make
- * that first call before any stream capture.  Calls share the array: calls
- * that overlap on the GPU race.  Synchronises the context's stream. */
+ * the last weight build), else STOKES_ERR_STATE.  The context's device must
+ * be the current device (else STOKES_ERR_ARG): the array's address is looked
+ * up on the first call on each device, with that device current.  Each call
+ * reads a status word back and synchronises the context's stream.  Calls
+ * share the array: calls that overlap on the GPU race.  The result z is
+ * bit-identical to stokes_apply_preconditioner(ctx, 2, r, z). */
 stokes_status stokes_apply_schwarz_noalloc(stokes_ctx ctx, const float* r, float* z);
 
 /* Number of tiles holding an active unknown (2D tiles are 32 x 8 slots,

@@ -761,10 +761,12 @@ cudaError_t schwarz_ensure(Ctx* c, const SchwarzPlan** plan) {
 // nothing, host or device.  The patch factors themselves are the context's
 // (built by an earlier Schwarz apply or solve).
 //
-// The array's device address is looked up once per device, with that device
-// current, on the first call on it; make that first call before any stream
-// capture.  Every call uses the same array: calls that overlap on the GPU
-// (other streams, other contexts, other threads) race and give wrong results.
+// The array's device address is looked up once per device, on the first call
+// on it, with the context's device current; a call made while another device
+// is current is refused.  Each call reads the solve status back and
+// synchronises the context's stream.  Every call uses the same array: calls
+// that overlap on the GPU (other streams, other contexts, other threads) race
+// and give wrong results.
 constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(8) << 20;   // 8 MiB: 2D grids up to about 540^2
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 constexpr int NOALLOC_MAX_DEVICES = 64;
@@ -805,6 +807,13 @@ cudaError_t apply_schwarz_noalloc(Ctx* c, const float* r, float* z, std::string*
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    // the symbol's address is per device, and the kernels run on the
+    // context's stream: both need the context's device current
+    if (dev != c->device) {
+        *why = "the context's device (" + std::to_string(c->device) + ") is not the current device (" +
+               std::to_string(dev) + "): make it current first";
+        return cudaErrorInvalidValue;
+    }
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) { *why = "device index out of range"; return cudaErrorInvalidDevice; }
     unsigned char* base = nullptr;
     {
@@ -825,7 +834,12 @@ cudaError_t apply_schwarz_noalloc(Ctx* c, const float* r, float* z, std::string*
     cudaStream_t s = c->stream;
     const int64_t V = c->vec_elems();
     // what must start at zero: the scalars (done, status), the counter and
-    // the local results (inactive patches and positions are summed as zeros)
+    // the local results (inactive patches and positions are summed as zeros).
+    // The scalars stay zero apart from what the kernels write: this call
+    // defines only z (the r.z and r.r the gather also forms are not returned),
+    // so it needs none of the CG parameters the existing entry point uploads.
+    // The kernels, their order and their inputs are those of that entry point,
+    // so z is bit-identical to its result.
     if ((e = cudaMemsetAsync(base, 0, lo.total, s)) != cudaSuccess) return e;
     // inactive tiles: identity on real slots (r is zero on padding)
     if ((e = cudaMemcpyAsync(z, r, sizeof(float) * V, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
