@@ -45,7 +45,7 @@ typedef enum {
     STOKES_ERR_NOT_CONVERGED = -3,  /* iteration cap reached above tolerance  */
     STOKES_ERR_BREAKDOWN = -4,      /* p.Ap <= 0 or r.z <= 0 in CG            */
     STOKES_ERR_TIMEOUT = -5,        /* a bounded device-side wait gave up     */
-    STOKES_ERR_BOUNDS = -6,         /* device-side index check failed         */
+    /* -6 is not used */
     STOKES_ERR_NONFINITE = -7,      /* NaN/Inf found in an input or residual  */
     STOKES_ERR_STATE = -8           /* call out of order (e.g. no weights)    */
 } stokes_status;
@@ -186,6 +186,12 @@ typedef struct {
                           while node); 0: host-driven chunks of check_every
                           iterations launched one kernel at a time (for
                           profilers that cannot enter conditional graphs)   */
+    int wait_test;     /* test hook for the bounded device-side waits, 0 in
+                          normal use.  1 (precond = 2, mixed mode): the
+                          Schwarz local solves wait for a factor copy that is
+                          never issued, giving up after 1,024 polls, so the
+                          call returns STOKES_ERR_TIMEOUT and the context
+                          stays usable.                                     */
 } stokes_options;
 
 typedef struct {
@@ -201,7 +207,7 @@ typedef struct {
 } stokes_stats;
 
 /* Fill ``o`` with defaults: FP64 mode, tol 1e-8, max_iter 200000,
- * inner_tol 1e-4, max_outer 40, check_every 64, Jacobi. */
+ * inner_tol 1e-4, max_outer 40, check_every 64, Jacobi, wait_test 0. */
 void stokes_default_options(stokes_options* o);
 
 /*

@@ -117,6 +117,7 @@ void stokes_default_options(stokes_options* o) {
     o->check_every = 64;
     o->precond = 0;
     o->use_graph = 1;
+    o->wait_test = 0;
 }
 
 const char* stokes_last_error(stokes_ctx ctx) {
@@ -355,6 +356,7 @@ static stokes_status check_opts(Ctx& c, const stokes_options* o) {
         c.err = "bad tolerances or caps";
         return STOKES_ERR_ARG;
     }
+    if (o->wait_test != 0 && o->wait_test != 1) { c.err = "wait_test must be 0 or 1"; return STOKES_ERR_ARG; }
     if (!c.have_weights) { c.err = "stokes_build_weights has not run"; return STOKES_ERR_STATE; }
     return STOKES_OK;
 }

@@ -82,6 +82,7 @@ struct Ctx {
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // inner solve per precision (+ Schwarz)
     LearnedState learned;
     long learned_jacobi_steps = 0;
+    int wait_test = 0;          // options.wait_test of the solve in progress (0 outside a solve)
     // additive Schwarz preconditioner (2D), rebuilt lazily after each weight build
     struct SchwarzPlan* sw = nullptr;
     std::vector<void*> sw_allocs;

@@ -47,6 +47,7 @@ struct CgScalars {
     double scale;           // inner right-hand side = scale * outer residual
     double tol_rel;         // relative recurrence tolerance of this solve
     int iter, done, status, max_iter;
+    int wait_test;          // test hook: the local solves wait for a copy never issued
 };
 
 enum { MODE_PLAIN = 0, MODE_RESID = 1, MODE_CG = 2 };

@@ -586,6 +586,7 @@ static cudaError_t push_inner_params(Ctx* c, double scale, double tol_rel, int m
     h.scale = scale;
     h.tol_rel = tol_rel;
     h.max_iter = max_iter;
+    h.wait_test = c->wait_test;
     return cudaMemcpyAsync(c->sc, &h, sizeof(CgScalars), cudaMemcpyHostToDevice, c->stream);
 }
 
@@ -608,6 +609,12 @@ stokes_status solve_system(Ctx* c, const double* b, double* x, const stokes_opti
         if (st) { st->iterations = 0; st->outer = 0; st->rel_residual = 0.0; st->status = 0; }
         return STOKES_OK;
     }
+    // the wait test hook holds for this solve only
+    struct WaitTestScope {
+        int& v;
+        ~WaitTestScope() { v = 0; }
+    } wait_scope{c->wait_test};
+    c->wait_test = o->wait_test;
     CgScalars* so = c->sc + 1;
     k_outer_init<<<nb, 256, 0, s>>>(L, c->tiles, c->nf, b, x, c->w64.r, so, c->partial, c->counter, nb);
     CK(cudaGetLastError());

@@ -289,7 +289,8 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
 // the threads gather, rotate and scale r_p into s.  Then the two triangular
 // products (sw_factor_products); rotate back and store by position.  A copy
 // that never completes (bounded wait) marks the solve STOKES_ERR_TIMEOUT and
-// ends it.
+// ends it.  With the test hook (sc->wait_test) no copy is issued, so the
+// wait runs out after SW_TEST_POLLS polls and nothing is left in flight.
 __global__ void __launch_bounds__(128, 15) k_schwarz_gemv(Layout L, SchwarzPlan P, const float* __restrict__ r,
                                                       CgScalars* sc) {
     extern __shared__ __align__(128) uint8_t Fs[];             // SW_FAC_BYTES
@@ -302,10 +303,11 @@ __global__ void __launch_bounds__(128, 15) k_schwarz_gemv(Layout L, SchwarzPlan 
     const int p = blockIdx.x;
     const uint32_t b_addr = smem_u32(&bar);
     const int n = P.nloc[p];
+    const bool stall = sc->wait_test != 0;
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_addr), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        sw_issue(b_addr, Fs, P.fac + (int64_t)p * SW_FAC_BYTES, sw_patch_bytes(n), P.evict_first != 0);
+        if (!stall) sw_issue(b_addr, Fs, P.fac + (int64_t)p * SW_FAC_BYTES, sw_patch_bytes(n), P.evict_first != 0);
     }
     constexpr float H = 0.70710678118654752f;
     const int I = P.corner[p] & 0xffff, J = P.corner[p] >> 16;
@@ -343,12 +345,12 @@ __global__ void __launch_bounds__(128, 15) k_schwarz_gemv(Layout L, SchwarzPlan 
         }
     }
     if (t >= n && t < (n + 7) / 8 * 8) s[t] = 0.f;    // the padded last block
-    if (t == 0) ok_s = mbar_wait(b_addr, 0) ? 1 : 0;
+    if (t == 0) ok_s = mbar_wait(b_addr, 0, stall ? SW_TEST_POLLS : SW_WAIT_POLLS) ? 1 : 0;
     __syncthreads();
     if (!ok_s) {
-        // give the copy one more bounded wait before the CTA leaves
+        // give an issued copy one more bounded wait before the CTA leaves
         if (t == 0) {
-            mbar_wait(b_addr, 0);
+            if (!stall) mbar_wait(b_addr, 0);
             sc->status = STOKES_ERR_TIMEOUT;
             sc->done = 1;
         }

@@ -62,10 +62,13 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 // Polls of the bulk copy's mbarrier before a local solve gives up (each
 // try_wait itself blocks for a while); the copy of 13 KB takes microseconds.
 constexpr long long SW_WAIT_POLLS = 1LL << 22;
+// Polls of the test hook's wait (options.wait_test): a copy that is never
+// issued, so the wait gives up after about a millisecond.
+constexpr long long SW_TEST_POLLS = 1024;
 
-// Wait for phase `parity` of an mbarrier, at most SW_WAIT_POLLS polls.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (long long i = 0; i < SW_WAIT_POLLS; ++i) {
+// Wait for phase `parity` of an mbarrier, at most `polls` polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long polls = SW_WAIT_POLLS) {
+    for (long long i = 0; i < polls; ++i) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libstokes.so")
 
 FP64, FP32, BF16 = 0, 1, 2
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_NOT_CONVERGED", -4: "ERR_BREAKDOWN",
-          -5: "ERR_TIMEOUT", -6: "ERR_BOUNDS", -7: "ERR_NONFINITE", -8: "ERR_STATE"}
+          -5: "ERR_TIMEOUT", -7: "ERR_NONFINITE", -8: "ERR_STATE"}
 
 
 class Grid(C.Structure):
@@ -31,7 +31,8 @@ class Layout(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("mode", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("inner_tol", C.c_double),
-                ("max_outer", C.c_int), ("check_every", C.c_int), ("precond", C.c_int), ("use_graph", C.c_int)]
+                ("max_outer", C.c_int), ("check_every", C.c_int), ("precond", C.c_int), ("use_graph", C.c_int),
+                ("wait_test", C.c_int)]
 
 
 class Stats(C.Structure):
