@@ -300,17 +300,7 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     wl = make_workload(args.workload, rank)
     ctx, d = stokes.context_for(wl)
-    nf = ctx.layout.nfields
-    n = wl.n
-    if wl.dim == 2:
-        sizes = [n[0] * n[1], (n[0] + 1) * (n[1] + 1), n[0] * n[1]]
-    else:
-        nx, ny, nz = n
-        sizes = [nx * ny * nz, nx * ny * nz, nz * (ny + 1) * (nx + 1), (nz + 1) * ny * (nx + 1),
-                 (nz + 1) * (ny + 1) * nx, nx * ny * nz]
-    u_out = [torch.zeros_like(t) for t in d["u_star"]]
-    taus = [torch.zeros(s, dtype=torch.float64, device=dev) for s in sizes[:-1]]
-    p = torch.zeros(sizes[-1], dtype=torch.float64, device=dev)
+    u_out, taus, p = _outputs(wl, d)
     precond = {"jacobi": 0, "schwarz": 2}[args.precond]
     if wl.dim != 2:
         precond = 0                    # the Schwarz preconditioner is 2D only
@@ -394,6 +384,8 @@ def run_ours(args, rank, world):
     apply_kernel = "k_apply2d" if wl.dim == 2 else "k_apply3d"
     apply_bytes = slots * bytes_per_slot_apply(wl.dim, prec)
     apply_gbs = apply_bytes / (ms_apply * 1e-3) / 1e9
+    active_slots = count_active_slots(ctx, wl)
+    active_bytes = active_slots * bytes_per_slot_apply(wl.dim, prec)
     if precond == 2:
         ms_local, ms_gather, local_bytes = ctx.bench_schwarz_kernels(50)
         achieved = local_bytes / (ms_local * 1e-3) / 1e9
@@ -412,6 +404,8 @@ def run_ours(args, rank, world):
                     "source_hash": kernel_source_hash(apply_kernel)}
     stencil = {"kernel": f"{apply_kernel} (CG mode)", "workload": args.workload, "achieved": apply_gbs,
                "unit": "GB/s", "frac": apply_gbs / peak, "ms_per_launch": ms_apply, "bytes_per_launch": apply_bytes,
+               "units_per_launch": f"{slots} slots of active tiles",
+               "active_slots": active_slots, "achieved_over_active_slots": active_bytes / (ms_apply * 1e-3) / 1e9,
                "update_ms_per_launch": ms_update}
     if not args.no_dense_apply:
         stencil["dense"] = [dense_apply(dim, n, pr, peak) for dim, n in ((2, 4096), (2, 1024), (3, 256))
@@ -433,12 +427,36 @@ def run_ours(args, rank, world):
                    "ms_schwarz_setup": ctx.schwarz_setup_ms() if precond == 2 else None,
                    "steps_per_s_all_ranks": world * 1000.0 / ms},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "velocity_error_vs_oracle": velocity_error(u_out, oracle_velocity_samples(args.workload)),
         "gpu_launches": launches * args.steps,
         "roofline": roofline,
         "stencil_apply": stencil,
         "clocks": clk.summary(),
+        "_ctx": (ctx, d),
     }
     return out, wl
+
+
+def count_active_slots(ctx, wl):
+    """Slots (i, j[, k]) holding at least one active unknown."""
+    act = ctx.export(3).cpu().numpy().astype(bool)
+    n = wl.n
+    if wl.dim == 2:
+        nx, ny = n
+        shapes = [(ny, nx), (ny + 1, nx + 1), (ny, nx)]
+        lat = np.zeros((ny + 1, nx + 1), dtype=bool)
+    else:
+        nx, ny, nz = n
+        shapes = [(nz, ny, nx), (nz, ny, nx), (nz, ny + 1, nx + 1), (nz + 1, ny, nx + 1), (nz + 1, ny + 1, nx),
+                  (nz, ny, nx)]
+        lat = np.zeros((nz + 1, ny + 1, nx + 1), dtype=bool)
+    o = 0
+    for shp in shapes:
+        m = int(np.prod(shp))
+        a = act[o:o + m].reshape(shp)
+        lat[tuple(slice(0, t) for t in shp)] |= a
+        o += m
+    return int(lat.sum())
 
 
 def dense_apply(dim, n, prec, peak):
@@ -470,70 +488,309 @@ def dense_apply(dim, n, prec, peak):
             "update_ms_per_launch": ms_u}
 
 
-def cpu_sample(wl, n_iter_fp64, budget_s=12.0,
-               count_source="the FP64 Jacobi-PCG count on the GPU for the same system"):
-    """Time the oracle as it stands on host cores: system build (fractions,
-    validity, explicit CSR assembly, right-hand side) once, a bounded number
-    of its Jacobi-PCG iterations, one recovery; extrapolate to the number of
-    FP64 PCG iterations the step needs."""
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def oracle_pcg_count(n):
+    """The oracle's own FP64 Jacobi-PCG iteration count to 1e-8 on the 2D
+    Gaussian-bump workload at n^2 (written by
+    tests/golden/make_oracle_pcg_counts.py, which runs only the oracle), and
+    the whole table for the report."""
+    path = os.path.join(GOLDEN, "oracle_pcg_counts.txt")
+    rows, head = {}, []
+    if os.path.exists(path):
+        for line in open(path):
+            if line.startswith("#"):
+                head.append(line[1:].strip())
+            elif line.strip():
+                f = line.split()
+                rows[int(f[0])] = dict(iterations=int(f[1]), rel_residual=float(f[2]), build_s=float(f[3]),
+                                       solve_s=float(f[4]), ms_per_iteration=float(f[5]), active=int(f[6]))
+    return rows.get(n, {}).get("iterations"), {"rows": rows, "header": head}
+
+
+def oracle_velocity_samples(name):
+    """(face indices, oracle velocities, scale) from
+    tests/golden/oracle_velocity_<name>.txt, or None."""
+    path = os.path.join(GOLDEN, f"oracle_velocity_{name}.txt")
+    if not os.path.exists(path):
+        return None
+    scale = None
+    idx, val = [], []
+    for line in open(path):
+        if line.startswith("# scale"):
+            scale = float(line.split(":")[1])
+        elif line.strip() and not line.startswith("#"):
+            a, b = line.split()
+            idx.append(int(a))
+            val.append(float(b))
+    return np.array(idx), np.array(val), scale
+
+
+def window_face_to_full(idx, n, win):
+    """Face indices of a window's face fields (u, v, w concatenated) to the
+    full n^3 grid's."""
+    i0, j0, k0, ni, nj, nk = win
+    wsh = [(nk, nj, ni + 1), (nk, nj + 1, ni), (nk + 1, nj, ni)]
+    fsh = [(n, n, n + 1), (n, n + 1, n), (n + 1, n, n)]
+    woff = np.cumsum([0] + [int(np.prod(t)) for t in wsh])
+    foff = np.cumsum([0] + [int(np.prod(t)) for t in fsh])
+    out = np.empty_like(idx)
+    for d in range(3):
+        m = (idx >= woff[d]) & (idx < woff[d + 1])
+        k, j, i = np.unravel_index(idx[m] - woff[d], wsh[d])
+        out[m] = foff[d] + np.ravel_multi_index((k + k0, j + j0, i + i0), fsh[d])
+    return out
+
+
+def velocity_error(u_fields, samples, index_map=None):
+    """Largest |u - u_oracle| over the stored samples, relative to the
+    oracle's largest live-face |u|."""
+    if samples is None:
+        return None
+    idx, val, scale = samples
+    u = np.concatenate([t.detach().cpu().numpy().ravel() for t in u_fields])
+    if index_map is not None:
+        idx = index_map(idx)
+    return float(np.abs(u[idx] - val).max() / scale)
+
+
+def host_cpu():
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return model, os.cpu_count()
+
+
+def cpu_sample(wl, n_iter, budget_s=8.0, count_source="", threads=None, S=None):
+    """Time the oracle as it stands on host cores: the system build
+    (fractions, validity, explicit CSR assembly, right-hand side) once, a
+    bounded number of its Jacobi-PCG iterations, one recovery; extrapolate to
+    ``n_iter`` iterations.  ``threads`` caps numpy's BLAS pool (None: the
+    default pool; scipy's sparse product runs on one thread either way)."""
+    from threadpoolctl import threadpool_limits
     from oracle import solve as So
     from oracle import system as S_
-    t0 = time.perf_counter()
-    S = S_.build_system(S_.StokesInput(**wl.as_oracle_kwargs()))
-    t_build = time.perf_counter() - t0
-    k = 5
-    t_it = So.time_pcg_iterations(S.A, S.b, k) / k
-    k2 = int(max(5, min(200, budget_s / max(t_it, 1e-6))))
-    t_it = So.time_pcg_iterations(S.A, S.b, k2) / k2
-    t0 = time.perf_counter()
-    S_.recover_velocity(S, np.zeros(S.A.shape[0]))
-    t_rec = time.perf_counter() - t0
-    est = t_build + n_iter_fp64 * t_it + t_rec
-    return {"value": est * 1000.0, "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": f"oracle build ({t_build:.1f} s) + {k2} Jacobi-PCG iterations ({t_it * 1e3:.1f} ms each) "
-                      f"+ recovery on the full system, extrapolated to {n_iter_fp64} iterations ({count_source})"}
+    t_build = None
+    if S is None:
+        t0 = time.perf_counter()
+        S = S_.build_system(S_.StokesInput(**wl.as_oracle_kwargs()))
+        t_build = time.perf_counter() - t0
+    with threadpool_limits(limits=threads):
+        k = 5
+        t_it = So.time_pcg_iterations(S.A, S.b, k) / k
+        k2 = int(max(5, min(400, budget_s / max(t_it, 1e-6))))
+        t_it = So.time_pcg_iterations(S.A, S.b, k2) / k2
+        t0 = time.perf_counter()
+        S_.recover_velocity(S, np.zeros(S.A.shape[0]))
+        t_rec = time.perf_counter() - t0
+    return S, t_build, t_it, t_rec, k2
 
 
-def fp64_iterations(wl, with_time=False):
-    """Plain FP64 Jacobi-PCG on the same system: iterations (and device ms)."""
+def cpu_baseline(wl, n, budget_s=8.0):
+    """The oracle on this host: build once, then bounded samples of its
+    Jacobi-PCG iterations on all host cores (default BLAS pool) and on one
+    thread, extrapolated to the oracle's own iteration count for this
+    workload."""
+    n_it, table = oracle_pcg_count(n)
+    model, ncpu = host_cpu()
+    if n_it is None:
+        return {"value": None, "unit": "ms", "kind": "oracle", "cores": ncpu,
+                "error": "no oracle iteration count for this workload in tests/golden/oracle_pcg_counts.txt"}
+    S, t_build, t_all, t_rec, k_all = cpu_sample(wl, n_it, budget_s)
+    _, _, t_one, _, k_one = cpu_sample(wl, n_it, budget_s, threads=1, S=S)
+    est = lambda t: (t_build + n_it * t + t_rec) * 1000.0
+    return {"value": est(t_all), "unit": "ms", "cores": ncpu, "kind": "oracle",
+            "sample": f"oracle build ({t_build:.1f} s), {k_all} of its FP64 Jacobi-PCG iterations "
+                      f"({t_all * 1e3:.2f} ms each) and one recovery on the full system, extrapolated to the "
+                      f"oracle's own {n_it} iterations to 1e-8 (tests/golden/oracle_pcg_counts.txt); "
+                      f"numpy's default BLAS pool on {ncpu} cores (the sparse product itself is one thread)",
+            "single_thread": {"value": est(t_one), "ms_per_iteration": t_one * 1e3, "iterations_sampled": k_one},
+            "ms_per_iteration": t_all * 1e3, "build_s": t_build, "iterations": n_it,
+            "cpu": model, "complete_solves_elsewhere": table}
+
+
+def gpu_plain_fp64(ctx, d):
+    """Plain FP64 Jacobi-PCG on the GPU on the same system (solve only)."""
     import torch
     from paper_1010_2832_gb300 import stokes
-    ctx, d = stokes.context_for(wl)
     b = ctx.new_vector()
     x = ctx.new_vector()
     ctx.rhs(d["u_star"], b)
     st = ctx.solve_system(b, x, stokes.default_options(mode=0, tol=1e-8))
     torch.cuda.synchronize()
-    if with_time:
-        return st.iterations, st.ms_solve, st.status
-    return st.iterations
+    return {"iterations": st.iterations, "ms_solve": st.ms_solve, "status": st.status,
+            "rel_residual": st.rel_residual, "note": "plain FP64 Jacobi-PCG on the same system (solve only)"}
+
+
+def _outputs(wl, d):
+    import torch
+    n = wl.n
+    dev = d["u_star"][0].device
+    if wl.dim == 2:
+        sizes = [n[0] * n[1], (n[0] + 1) * (n[1] + 1), n[0] * n[1]]
+    else:
+        nx, ny, nz = n
+        sizes = [nx * ny * nz, nx * ny * nz, nz * (ny + 1) * (nx + 1), (nz + 1) * ny * (nx + 1),
+                 (nz + 1) * (ny + 1) * nx, nx * ny * nz]
+    u_out = [torch.zeros_like(t) for t in d["u_star"]]
+    taus = [torch.zeros(s, dtype=torch.float64, device=dev) for s in sizes[:-1]]
+    p = torch.zeros(sizes[-1], dtype=torch.float64, device=dev)
+    return u_out, taus, p
+
+
+def config_column256(args, flush):
+    """The 3D 256^3 falling column: the mixed-precision step (weights, right-
+    hand side, FP32 Jacobi-CG in FP64 refinement, recovery) timed like the
+    headline step, the same step in plain FP64 PCG, and both velocities
+    against the oracle on the column's liquid window."""
+    import torch
+    from paper_1010_2832_gb300 import stokes, workloads as W
+    wl = W.column_3d(256)
+    ctx, d = stokes.context_for(wl)
+    u_out, taus, p = _outputs(wl, d)
+    samples = oracle_velocity_samples("column256")
+    win = (111, 0, 111, 34, 160, 34)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": "column256", "desc": WORKLOADS["column256"]["desc"]}
+    for name, opt in (("mixed_fp32_jacobi", stokes.default_options(mode=1, tol=1e-8)),
+                      ("plain_fp64_pcg", stokes.default_options(mode=0, tol=1e-8))):
+        times, stats = [], []
+        for k in range(2 + 3):
+            flush.fill_(float(k))
+            ev0.record()
+            ctx.build_weights(d["phi_liquid"], d["phi_solid"], d["rho"], d["mu"], d["u_bc"])
+            st = ctx.solve_step(d["u_star"], u_out, taus, p, opt)
+            ev1.record()
+            torch.cuda.synchronize()
+            if k >= 2:
+                times.append(ev0.elapsed_time(ev1))
+                stats.append(st.as_dict())
+        out[name] = {"ms_per_step": float(np.mean(times)), "iterations": stats[-1]["iterations"],
+                     "outer": stats[-1]["outer"], "rel_residual": stats[-1]["rel_residual"],
+                     "status": stats[-1]["status"], "ms_solve": float(np.mean([s["ms_solve"] for s in stats])),
+                     "velocity_error_vs_oracle": velocity_error(
+                         u_out, samples, lambda i: window_face_to_full(i, 256, win))}
+    ctx.close()
+    del u_out, taus, p, d
+    torch.cuda.empty_cache()
+    out["note"] = ("3 timed steps after 2 warm-up steps each, weights included, L2 flushed; velocity error = max "
+                   "over 4,096 oracle samples on the liquid window of |u - u_oracle| / max|u_oracle|")
+    return out
+
+
+def config_batch64(args):
+    """64 uneven 2D instances: the batched step (persistent FP64 Schwarz-PCG
+    under a CUDA graph) against the same instances one after another with
+    plain FP64 Jacobi-PCG and with the single-instance mixed Schwarz-CG."""
+    import torch
+    from paper_1010_2832_gb300 import stokes, workloads as W
+    wls = W.batch_instances(count=64, seed0=4000)
+    made = [stokes.context_for(wl) for wl in wls]
+    ctxs = [m[0] for m in made]
+    devs = [m[1] for m in made]
+    batch = stokes.Batch(ctxs, stokes.default_options(mode=0, tol=1e-8, precond=2))
+    o = [_outputs(wl, d) for wl, d in zip(wls, devs)]
+    args_io = ([d["u_star"] for d in devs], [x[0] for x in o], [x[1] for x in o], [x[2] for x in o])
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    batch.solve(*args_io)
+    times = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        ev0.record()
+        for c, d in zip(ctxs, devs):
+            c.build_weights(d["phi_liquid"], d["phi_solid"], d["rho"], d["mu"], d["u_bc"])
+        stats, ms = batch.solve(*args_io)
+        ev1.record()
+        torch.cuda.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+    res = {"workload": "batch64", "desc": WORKLOADS["batch64"]["desc"],
+           "batched_fp64_schwarz": {"ms_per_step": float(np.mean(times)),
+                                    "iterations_max": max(s["iterations"] for s in stats),
+                                    "failed": sum(1 for s in stats if s["status"] != 0),
+                                    "worst_rel_residual": max(s["rel_residual"] for s in stats),
+                                    "tuning": batch.tuning()}}
+    batch.close()
+    for name, opt in (("one_by_one_plain_fp64_pcg", stokes.default_options(mode=0, tol=1e-8, precond=0)),
+                      ("one_by_one_mixed_fp32_schwarz", stokes.default_options(mode=1, tol=1e-8, precond=2))):
+        total, its, bad = 0.0, [], 0
+        for c, d, oo in zip(ctxs, devs, o):
+            ev0.record()
+            c.build_weights(d["phi_liquid"], d["phi_solid"], d["rho"], d["mu"], d["u_bc"])
+            st = c.solve_step(d["u_star"], oo[0], oo[1], oo[2], opt)
+            ev1.record()
+            torch.cuda.synchronize()
+            total += ev0.elapsed_time(ev1)
+            its.append(st.iterations)
+            bad += st.status != 0
+        res[name] = {"ms_sum": total, "iterations_max": max(its), "failed": bad}
+    for c in ctxs:
+        c.close()
+    torch.cuda.empty_cache()
+    res["note"] = "weights included in every form; batched: mean of 2 steps after one warm-up"
+    return res
 
 
 def run_reference(args):
-    """The oracle timed on host cores (the reference arm of this build)."""
-    from paper_1010_2832_gb300 import workloads as W  # noqa: F401
-    wl = make_workload(args.workload, 0)
-    n_it = None
-    source = "the FP64 Jacobi-PCG count on the GPU for the same system"
-    try:
-        n_it = fp64_iterations(wl)
-    except Exception:
-        n_it = None
+    """The oracle timed on host cores (the reference arm of this build): no
+    GPU and no library of this package; the input generators only."""
+    from paper_1010_2832_gb300 import workloads as W  # seeded inputs, no method arithmetic
+    from oracle import solve as So
+    from oracle import system as S_
+    if args.workload != "bumps1024":
+        return {"impl": "reference", "unavailable": "the oracle's iteration count is recorded for the 2D "
+                                                    "Gaussian-bump workload only"}
+    n = args.ref_size
+    wl = W.bumps_2d(n, seed=2)
+    n_it, table = oracle_pcg_count(n)
+    model, ncpu = host_cpu()
     if n_it is None:
-        n_it = 20000
-        source = "a fixed count: no GPU to measure the FP64 Jacobi-PCG count, which is about 1.6e5 on this system"
-    vals = []
+        return {"impl": "reference", "unavailable": f"tests/golden/oracle_pcg_counts.txt holds no {n}^2 count"}
+    t0 = time.perf_counter()
+    S = S_.build_system(S_.StokesInput(**wl.as_oracle_kwargs()))
+    t_build = time.perf_counter() - t0
+    vals, per_it = [], []
     for k in range(args.warmup + args.steps):
-        s = cpu_sample(wl, n_it, budget_s=3.0, count_source=source)
+        _, _, t_it, t_rec, k2 = cpu_sample(wl, n_it, budget_s=2.0, S=S)
         if k >= args.warmup:
-            vals.append(s["value"])
+            per_it.append(t_it)
+            vals.append((t_build + n_it * t_it + t_rec) * 1000.0)
     v = float(np.mean(vals))
+    # complete oracle solves on this host: config 1 (32^2 disk, FP64 PCG to
+    # 1e-10) and the bump workload at a small size (to 1e-8), on all cores
+    # and on one
+    from threadpoolctl import threadpool_limits
+    complete = {}
+    nb = args.ref_complete_size
+    for label, wlc, tol in (("disk32_config1", W.disk_in_box(32, seed=1), 1e-10),
+                            (f"bumps{nb}", W.bumps_2d(nb, seed=2), 1e-8)):
+        Sc = S_.build_system(S_.StokesInput(**wlc.as_oracle_kwargs()))
+        for th_name, th in (("all_cores", None), ("one_thread", 1)):
+            with threadpool_limits(limits=th):
+                t0 = time.perf_counter()
+                _, it, rel = So.pcg(Sc.A, Sc.b, tol=tol, max_iter=10 ** 7)
+                complete[f"{label}_{th_name}"] = {"ms": (time.perf_counter() - t0) * 1e3, "iterations": it,
+                                                  "rel_residual": rel}
+    sample = (f"oracle build ({t_build:.1f} s, once) + per step a bounded sample of its FP64 Jacobi-PCG iterations "
+              f"on the full {n}^2 system ({np.mean(per_it) * 1e3:.2f} ms each), extrapolated to the oracle's own "
+              f"{n_it} iterations to 1e-8 (tests/golden/oracle_pcg_counts.txt); numpy's default BLAS pool on "
+              f"{ncpu} cores (the sparse product is one thread)")
     return {"impl": "reference", "metric": "time-to-solution per implicit step at 1e-8 rel. residual", "value": v,
             "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)", "config": {"workload": args.workload,
                                                      "desc": WORKLOADS[args.workload]["desc"]},
-            "cpu_baseline": dict(s, value=v),
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": ncpu, "kind": "oracle", "sample": sample,
+                             "cpu": model, "complete_solves": complete,
+                             "complete_solves_elsewhere": table},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -550,6 +807,9 @@ def main():
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the 3D column and 64-instance batch lines")
+    ap.add_argument("--ref-size", type=int, default=1024, help=argparse.SUPPRESS)
+    ap.add_argument("--ref-complete-size", type=int, default=128, help=argparse.SUPPRESS)
     ap.add_argument("--no-dense-apply", action="store_true", help="skip the dense-box apply measurement")
     ap.add_argument("--quick", action="store_true", help="timed steps only (for profiler runs)")
     ap.add_argument("--no-graph", action="store_true",
@@ -558,6 +818,7 @@ def main():
     if args.quick:
         args.no_cpu_baseline = True
         args.no_dense_apply = True
+        args.no_configs = True
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
@@ -576,13 +837,24 @@ def main():
             torch.distributed.destroy_process_group()
         return
     out, wl = run_ours(args, rank, world)
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.quick:
         try:
-            n_it, ms64, st64 = fp64_iterations(wl, with_time=True)
-            out["plain_fp64_pcg"] = {"iterations": n_it, "ms_solve": ms64, "status": st64,
-                                     "note": "plain FP64 Jacobi-PCG on the same system (solve only)"}
-            out["cpu_baseline"] = cpu_sample(wl, n_it)
-            out["solver"]["fp64_pcg_iterations"] = n_it
+            out["plain_fp64_pcg"] = gpu_plain_fp64(*out.pop("_ctx"))
+            out["solver"]["fp64_pcg_iterations"] = out["plain_fp64_pcg"]["iterations"]
+        except Exception as e:  # a baseline must not hide the GPU result
+            out["plain_fp64_pcg"] = {"error": repr(e)}
+    out.pop("_ctx", None)
+    if rank == 0 and not args.quick and not args.no_configs and args.workload == "bumps1024":
+        flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
+        out["configs"] = {}
+        for key, fn in (("column256", lambda: config_column256(args, flush)), ("batch64", lambda: config_batch64(args))):
+            try:
+                out["configs"][key] = fn()
+            except Exception as e:
+                out["configs"][key] = {"error": repr(e)}
+    if rank == 0 and not args.no_cpu_baseline and wl.dim == 2 and args.workload == "bumps1024":
+        try:
+            out["cpu_baseline"] = cpu_baseline(wl, wl.n[0])
         except Exception as e:  # the baseline must not hide the GPU result
             out["cpu_baseline"] = {"value": None, "error": repr(e)}
     if rank == 0:
