@@ -145,7 +145,7 @@ __device__ void tile_report(double v0, double v1, double* part, int w, BState* s
 // FP64 (alpha = 0 outside a CG step).  Thread 0 starts the bulk copy of the
 // factor and waits on the CTA's mbarrier (phase parity = uses & 1, bounded);
 // a copy that never completes sets the batch's error flag.
-__device__ void batched_local_solve(const BInst& I, int p, double alpha, uint8_t* Fs, float* s, float* y,
+__device__ void batched_local_solve(const BInst& I, int p, double alpha, uint8_t* Fs, float* s, float* y, __half* hb,
                                     unsigned long long* bar, uint32_t& uses, int& ok_s, BGlobal* g) {
     const SchwarzPlan& P = I.sw;
     const Layout& L = I.L;
@@ -203,7 +203,7 @@ __device__ void batched_local_solve(const BInst& I, int p, double alpha, uint8_t
         __syncthreads();
         return;
     }
-    sw_factor_products(Fs, n, s, y);
+    sw_factor_products(Fs, n, s, y, hb);
     float* out = P.ybuf + (int64_t)(CJ * P.npx + CI) * PMAX;
     if (t < 2 * PR * PR) {
         const int e = t;
@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(256) k_batched(const BInst* __restrict__ inst,
     uint8_t* Fs = reinterpret_cast<uint8_t*>(smraw);
     __shared__ __align__(16) float ls[SW ? PMAX8 : 4];
     __shared__ float ly[SW ? PMAX : 4];
+    __shared__ __align__(16) __half lhb[SW ? 2 * 16 * 7 : 8];
     __shared__ __align__(8) unsigned long long lbar;
     __shared__ int lok;
     uint32_t uses = 0;
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(256) k_batched(const BInst* __restrict__ inst,
                 volatile BState* vs = st + i;
                 if (vs->done) continue;
                 const double alpha = vs->mode == 0 ? vs->alpha : 0.0;
-                batched_local_solve(inst[i], pl_patch[k], alpha, Fs, ls, ly, &lbar, uses, lok, g);
+                batched_local_solve(inst[i], pl_patch[k], alpha, Fs, ls, ly, lhb, &lbar, uses, lok, g);
             }
             if (!grid_sync(g, nb)) return;
         }

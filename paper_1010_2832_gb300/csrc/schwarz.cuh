@@ -287,7 +287,8 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
 // active patch.  Thread 0 starts a bulk (TMA) copy of the stored factor
 // (13 KB at most) into shared memory, completing on an mbarrier; meanwhile
 // the threads gather, rotate and scale r_p into s.  Then the two triangular
-// products (sw_factor_products); rotate back and store by position.  A copy
+// products on the tensor cores (sw_factor_products); rotate back and store
+// by position.  A copy
 // that never completes (bounded wait) marks the solve STOKES_ERR_TIMEOUT and
 // ends it.  With the test hook (sc->wait_test) no copy is issued, so the
 // wait runs out after SW_TEST_POLLS polls and nothing is left in flight.
@@ -296,6 +297,7 @@ __global__ void __launch_bounds__(128, 15) k_schwarz_gemv(Layout L, SchwarzPlan 
     extern __shared__ __align__(128) uint8_t Fs[];             // SW_FAC_BYTES
     __shared__ __align__(16) float s[PMAX8];
     __shared__ float y[PMAX];
+    __shared__ __align__(16) __half hb[2 * 16 * 7];
     __shared__ __align__(8) unsigned long long bar;
     __shared__ int ok_s;
     if (sc->done) return;
@@ -356,7 +358,7 @@ __global__ void __launch_bounds__(128, 15) k_schwarz_gemv(Layout L, SchwarzPlan 
         }
         return;
     }
-    sw_factor_products(Fs, n, s, y);
+    sw_factor_products(Fs, n, s, y, hb);
     // scale, rotate back and store by position
     float* out = P.ybuf + (int64_t)(J * P.npx + I) * PMAX;
     if (t < 2 * PR * PR) {

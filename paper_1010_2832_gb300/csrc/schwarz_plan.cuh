@@ -115,63 +115,187 @@ inline bool sw_factors_exceed_l2(size_t bytes) {
     return l2 > 0 && bytes > (size_t)l2 / 2;
 }
 
-// s <- X~^T diag(rho^2) X~ s for the stored factor F of an n-unknown patch in
-// shared memory (at least 128 threads).  y = X~ s: thread t takes row t, 16-byte loads
-// of eight FP16 entries; y_t *= rho_t^2; z = X~^T y: eight threads per block
-// of eight columns, each taking every eighth row, joined by shuffles.  s
-// holds PMAX8 floats, zero from n up to the next multiple of 8; y holds PMAX
-// floats of scratch.  Ends after a barrier with z in s[0, n).
-__device__ __forceinline__ void sw_factor_products(const uint8_t* F, int n, float* s, float* y) {
-    const int t = threadIdx.x;
-    const float* rs = reinterpret_cast<const float*>(F);
-    const __half* X = reinterpret_cast<const __half*>(F + SW_RS_BYTES);
-    if (t < n) {
-        const uint4* xr = reinterpret_cast<const uint4*>(X + tri8_off(t));
-        const float4* s4 = reinterpret_cast<const float4*>(s);
-        float acc = 0.f;
-        for (int j = 0; j <= t / 8; ++j) {
-            const uint4 a = xr[j];
-            const float4 b0 = s4[2 * j], b1 = s4[2 * j + 1];
-            float2 f = __half22float2(*reinterpret_cast<const __half2*>(&a.x));
-            acc = fmaf(f.x, b0.x, acc);
-            acc = fmaf(f.y, b0.y, acc);
-            f = __half22float2(*reinterpret_cast<const __half2*>(&a.y));
-            acc = fmaf(f.x, b0.z, acc);
-            acc = fmaf(f.y, b0.w, acc);
-            f = __half22float2(*reinterpret_cast<const __half2*>(&a.z));
-            acc = fmaf(f.x, b1.x, acc);
-            acc = fmaf(f.y, b1.y, acc);
-            f = __half22float2(*reinterpret_cast<const __half2*>(&a.w));
-            acc = fmaf(f.x, b1.z, acc);
-            acc = fmaf(f.y, b1.w, acc);
-        }
-        y[t] = acc * rs[t];
+// ---- the two triangular products on the tensor cores ---------------------
+// mma.sync m16n8k16, FP16 operands, FP32 accumulation.  The FP32 vector is
+// scaled by a power of two (largest magnitude into [2^13, 2^14)) and split
+// into FP16 hi + lo parts, which fill columns 0 and 1 of the B operand:
+// products of FP16 numbers are exact in FP32, so X~ (v_hi + v_lo) carries
+// the vector to about 2^-22 of its largest entry, as the FP32 path did.
+__device__ __forceinline__ void mma_f16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t (&a)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&a)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+                 : "r"(addr));
+}
+
+// Power of two putting a largest magnitude m into [2^13, 2^14) (shift
+// clamped to +-120): v * sc is split into FP16 hi + lo, results are scaled
+// back by inv = 1 / sc.
+__device__ __forceinline__ void sw_hl_scale(float m, float& sc, float& inv) {
+    const int e = m > 0.f ? ((__float_as_int(m) >> 23) & 0xff) - 127 : 0;
+    const int k = max(-120, min(120, 13 - e));
+    sc = __int_as_float((127 + k) << 23);
+    inv = __int_as_float((127 - k) << 23);
+}
+
+// Largest |v[k]| over k < n, reduced by every warp on its own.
+__device__ __forceinline__ float sw_warp_absmax(const float* v, int n, int lane) {
+    unsigned m = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = lane + 32 * q;
+        if (k < n) m = max(m, __float_as_uint(fabsf(v[k])));
     }
+    return __uint_as_float(__reduce_max_sync(0xffffffffu, m));
+}
+
+// Split of the vector v (n entries, scaled by sc) into FP16 hi + lo parts,
+// one entry per thread (threads 0..111), into hb[0][.] and hb[1][.]; entries
+// from n to 111 are zero.
+__device__ __forceinline__ void sw_split(const float* v, int n, float sc, __half* hb) {
+    const int t = threadIdx.x;
+    if (t < 16 * 7) {
+        const float x = t < n ? v[t] * sc : 0.f;
+        const __half hi = __float2half_rn(x);
+        hb[t] = hi;
+        hb[16 * 7 + t] = __float2half_rn(x - __half2float(hi));
+    }
+}
+
+// B fragment of k-tile kt from the split vector: lane (g, t) = (lane / 4,
+// lane % 4) holds B[2t, 2t+1][g] and B[2t+8, 2t+9][g]; column 0 is the hi
+// part, column 1 the lo part, columns 2..7 zero.
+__device__ __forceinline__ void sw_b_frag(const __half* hb, int kt, int lane, uint32_t& b0, uint32_t& b1) {
+    const int g = lane >> 2, t = lane & 3;
+    if (g < 2) {
+        const uint32_t* p = reinterpret_cast<const uint32_t*>(hb + 16 * 7 * g + 16 * kt + 2 * t);
+        b0 = p[0];
+        b1 = p[4];
+    } else {
+        b0 = b1 = 0u;
+    }
+}
+
+// s <- X~^T diag(rho^2) X~ s for the stored factor F of an n-unknown patch in
+// shared memory, by warps 0-3 of the CTA (every thread of the CTA must call
+// it).  X~ is cut into 16 x 16 tiles (rows and columns up to 112); tiles
+// wholly above the diagonal are skipped and the upper 8 x 8 block of each
+// diagonal tile (not stored: rows of the first half hold 8 columns fewer) is
+// zeroed in the fragment.  y = X~ s: output tile m costs m + 1 tile
+// products, so warps 0..3 take tiles {6}, {5, 0}, {4, 1}, {3, 2} (7 each,
+// the two chains of a warp interleaved); z = X~^T (rho^2 y): output tile c
+// costs 7 - c, so {0}, {1, 6}, {2, 5}, {3, 4}.  Tile addresses of rows at
+// or past n point at row 0 (finite data): their outputs are dropped (first
+// product) or meet zero vector entries (second product).  Each vector is
+// split into FP16 hi + lo once, one entry per thread, into hb (2 x 112
+// halves of shared memory).  s holds PMAX8 floats (entries from n on are
+// not read); y holds PMAX floats of scratch.  Ends after a barrier with z in
+// s[0, n).
+__device__ __forceinline__ void sw_factor_products(const uint8_t* F, int n, float* s, float* y, __half* hb) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float* rs = reinterpret_cast<const float*>(F);
+    const uint32_t X = smem_u32(F + SW_RS_BYTES);
+    const int g = lane >> 2, t = lane & 3;
+    const int li = lane >> 3, lj = lane & 7;      // ldmatrix: matrix li, its row lj
+    const int ntile = (n + 15) >> 4;
+    float sc = 1.f, inv = 1.f;
+    if (warp < 4) sw_hl_scale(sw_warp_absmax(s, n, lane), sc, inv);
+    sw_split(s, n, sc, hb);
     __syncthreads();
-    const int cb = t >> 3, q = t & 7;
-    float z[8];
+    if (warp < 4) {
+        const int mA = 6 - warp, mB = warp - 1;           // mB < mA; mB = -1 for warp 0
+        float dA[4] = {0.f, 0.f, 0.f, 0.f}, dB[4] = {0.f, 0.f, 0.f, 0.f};
+        int rowA = 16 * mA + (li & 1) * 8 + lj, rowB = 16 * max(mB, 0) + (li & 1) * 8 + lj;
+        rowA = rowA < n ? rowA : 0;
+        rowB = rowB < n ? rowB : 0;
+        const uint32_t baseA = X + 2u * (uint32_t)(tri8_off(rowA) + (li >> 1) * 8);
+        const uint32_t baseB = X + 2u * (uint32_t)(tri8_off(rowB) + (li >> 1) * 8);
+        const bool onA = mA < ntile, onB = mB >= 0 && mB < ntile;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) z[k] = 0.f;
-    if (8 * cb < n)
-        for (int row = 8 * cb + q; row < n; row += 8) {
-            const uint4 a = *reinterpret_cast<const uint4*>(X + tri8_off(row) + 8 * cb);
-            const float yr = y[row];
-            const uint32_t w[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[k]));
-                z[2 * k] = fmaf(f.x, yr, z[2 * k]);
-                z[2 * k + 1] = fmaf(f.y, yr, z[2 * k + 1]);
+        for (int kt = 0; kt < 7; ++kt) {
+            if (kt >= ntile) break;
+            uint32_t b0, b1;
+            sw_b_frag(hb, kt, lane, b0, b1);
+            if (onA && kt <= mA) {
+                uint32_t a[4];
+                ldsm_x4(a, baseA + 32u * kt);
+                if (kt == mA) a[2] = 0u;                 // upper 8 x 8 block of the diagonal tile
+                mma_f16_16816(dA, a, b0, b1);
+            }
+            if (onB && kt <= mB) {
+                uint32_t a[4];
+                ldsm_x4(a, baseB + 32u * kt);
+                if (kt == mB) a[2] = 0u;
+                mma_f16_16816(dB, a, b0, b1);
             }
         }
+        if (t == 0) {
+            if (onA) {
+                const int r0 = 16 * mA + g, r1 = r0 + 8;
+                if (r0 < n) y[r0] = (dA[0] + dA[1]) * inv * rs[r0];
+                if (r1 < n) y[r1] = (dA[2] + dA[3]) * inv * rs[r1];
+            }
+            if (onB) {
+                const int r0 = 16 * mB + g, r1 = r0 + 8;
+                if (r0 < n) y[r0] = (dB[0] + dB[1]) * inv * rs[r0];
+                if (r1 < n) y[r1] = (dB[2] + dB[3]) * inv * rs[r1];
+            }
+        }
+    }
+    __syncthreads();
+    if (warp < 4) sw_hl_scale(sw_warp_absmax(y, n, lane), sc, inv);
+    sw_split(y, n, sc, hb);          // hb of the first product is no longer read
+    __syncthreads();
+    if (warp < 4) {
+        const int cA = warp, cB = 7 - warp;               // cB = 7 (none) for warp 0
+        float dA[4] = {0.f, 0.f, 0.f, 0.f}, dB[4] = {0.f, 0.f, 0.f, 0.f};
+        const int cofsA = 16 * cA + (li & 1) * 8, cofsB = 16 * min(cB, 6) + (li & 1) * 8;
+        const bool onA = cA < ntile, onB = cB <= 6 && cB < ntile;
 #pragma unroll
-    for (int o = 1; o <= 4; o <<= 1)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) z[k] += __shfl_xor_sync(0xffffffffu, z[k], o);
-    // s is no longer read (y = X~ s ended at the barrier above)
-    if (q == 0 && 8 * cb < n) {
-        reinterpret_cast<float4*>(s)[2 * cb] = make_float4(z[0], z[1], z[2], z[3]);
-        reinterpret_cast<float4*>(s)[2 * cb + 1] = make_float4(z[4], z[5], z[6], z[7]);
+        for (int rt = 0; rt < 7; ++rt) {
+            if (rt >= ntile) break;
+            uint32_t b0, b1;
+            sw_b_frag(hb, rt, lane, b0, b1);
+            int row = 16 * rt + (li >> 1) * 8 + lj;
+            row = row < n ? row : 0;
+            const uint32_t rb = X + 2u * (uint32_t)tri8_off(row);
+            if (onA && rt >= cA) {
+                uint32_t a[4];
+                ldsm_x4_trans(a, rb + 2u * cofsA);
+                if (rt == cA) a[1] = 0u;                 // upper 8 x 8 block of the diagonal tile
+                mma_f16_16816(dA, a, b0, b1);
+            }
+            if (onB && rt >= cB) {
+                uint32_t a[4];
+                ldsm_x4_trans(a, rb + 2u * cofsB);
+                if (rt == cB) a[1] = 0u;
+                mma_f16_16816(dB, a, b0, b1);
+            }
+        }
+        if (t == 0) {
+            // s is no longer read (it was split into hb before the first barrier)
+            if (onA) {
+                const int c0 = 16 * cA + g, c1 = c0 + 8;
+                if (c0 < n) s[c0] = (dA[0] + dA[1]) * inv;
+                if (c1 < n) s[c1] = (dA[2] + dA[3]) * inv;
+            }
+            if (onB) {
+                const int c0 = 16 * cB + g, c1 = c0 + 8;
+                if (c0 < n) s[c0] = (dB[0] + dB[1]) * inv;
+                if (c1 < n) s[c1] = (dB[2] + dB[3]) * inv;
+            }
+        }
     }
     __syncthreads();
 }

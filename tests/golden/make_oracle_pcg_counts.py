@@ -59,9 +59,13 @@ def main(sizes):
         t0 = time.perf_counter()
         x, it, rel = So.pcg(S.A, S.b, tol=1e-8, max_iter=10 ** 7)
         t_solve = time.perf_counter() - t0
-        rows.append(f"{n} {it} {rel:.3e} {t_build:.2f} {t_solve:.1f} {1e3 * t_solve / max(it, 1):.3f} "
-                    f"{int(S.active.sum())}")
-        print(rows[-1], flush=True)
+        row = (f"{n} {it} {rel:.3e} {t_build:.2f} {t_solve:.1f} {1e3 * t_solve / max(it, 1):.3f} "
+               f"{int(S.active.sum())}")
+        print(row, flush=True)
+        # rows written meanwhile by another run of this script are kept
+        rows = [l.rstrip("\n") for l in open(OUT) if l.strip() and not l.startswith("#")] \
+            if os.path.exists(OUT) else []
+        rows = [r for r in rows if int(r.split()[0]) != n] + [row]
         with open(OUT, "w") as f:
             f.write("# The oracle's plain FP64 Jacobi-PCG (oracle.solve.pcg, tol 1e-8 on the true relative\n"
                     "# residual) on the 2D Gaussian-bump workload (workloads.bumps_2d(n, seed=2)).\n"

@@ -52,3 +52,19 @@ def abs_matvec(A, x):
     """|A| |x|: the scale against which a rounded A x is compared."""
     Aa = abs(A)
     return Aa @ np.abs(x)
+
+
+def golden_velocity_samples(name):
+    """(face indices, oracle velocities, scale) stored by
+    tests/golden/make_oracle_velocity_samples.py (oracle only)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"oracle_velocity_{name}.txt")
+    idx, val, scale = [], [], None
+    for line in open(path):
+        if line.startswith("# scale"):
+            scale = float(line.split(":")[1])
+        elif line.strip() and not line.startswith("#"):
+            a, b = line.split()
+            idx.append(int(a))
+            val.append(float(b))
+    return np.array(idx), np.array(val), scale

@@ -9,7 +9,13 @@ Tolerances (per entry, against the scale |A| |x| of the rounded sum):
   FP64 apply: 1e-13; FP32 apply: 1e-5 (a few float roundings per term);
   BF16 coefficients: 2e-2 (up to three 8-bit-mantissa factors per term).
 Solves: FP64 PCG velocities within 1e-9 of the oracle's direct solve
-(relative to max |u|); mixed precision reaches the same 1e-8 true residual.
+(relative to max |u|); mixed precision reaches the same 1e-8 true residual,
+and its velocities are within a per-case tolerance of the direct solve:
+ten times the error measured on a GB300, rounded up (VEL_TOL_MIXED).  At a
+1e-8 residual the error is set by the stopping test, not by the inner
+precision: plain FP64 PCG stopped at 1e-8 is off by the same amount
+(measured 5e-10 .. 4e-6 across these cases, FP32 and BF16 inner solves
+5e-10 .. 2.5e-6).
 """
 import numpy as np
 import pytest
@@ -42,6 +48,12 @@ def _cases():
 
 
 CASES = _cases()
+# max |u - u_oracle| / max |u_oracle| allowed for the mixed-precision solves
+# at a 1e-8 true residual (FP32 and BF16 inner CG): ten times the larger of
+# the two measured errors, rounded up
+VEL_TOL_MIXED = {"disk32": 3e-6, "rand2d_a": 3e-5, "rand2d_b": 3e-5, "bumps96": 4e-6, "bumps70_split": 2e-6,
+                 "rand3d_a": 3e-6, "rand3d_b": 6e-6, "column3d": 3e-8, "bumps3d": 4e-6, "paper_disk40": 2e-7,
+                 "paper_annulus48": 3e-6, "jet150_floor": 6e-9, "bumps96_floor": 8e-7}
 # floor of the live faces' mass fraction (stokes_set_min_face_liquid) per case;
 # the jet's opening puts level-set zeros on lattice points (1e-15 slivers)
 FLOORS = {"jet150_floor": 0.01, "bumps96_floor": 0.05}
@@ -179,9 +191,8 @@ def test_mixed_precision_reaches_fp64_residual(name, mode):
     u_ref = S_.recover_velocity(S, x_ref)
     lv = S.live
     umax = max(np.abs(u_ref[lv]).max(), 1e-30)
-    # a 1e-8 residual bounds the velocity error by cond(A) * 1e-8; report it
     err = np.abs(u - u_ref)[lv].max() / umax
-    assert err <= 1e-3, err
+    assert err <= VEL_TOL_MIXED[name], err
 
 
 def test_no_liquid_gives_zero_solution():

@@ -74,4 +74,7 @@ def test_schwarz_solve_reaches_fp64_residual_with_fewer_iterations(name):
     u_ref = S_.recover_velocity(S, x_ref)
     u = torch.cat([a.reshape(-1) for a in out[0]]).cpu().numpy()
     lv = S.live
-    assert np.abs(u - u_ref)[lv].max() <= 1e-3 * np.abs(u_ref[lv]).max()
+    # ten times the error measured on a GB300 (bumps40 2.1e-8, rand37x23
+    # 1.8e-7): set by the 1e-8 stopping test, as for plain FP64 PCG
+    tol = {"bumps40": 3e-7, "rand37x23": 2e-6}[name]
+    assert np.abs(u - u_ref)[lv].max() <= tol * np.abs(u_ref[lv]).max()
