@@ -11,18 +11,22 @@
 // nearest-neighbour up, concatenation [upsampled, skip].  In 2D, KZ = 1 and
 // D = 1.
 //
-// Kernels: direct convolution (one output voxel per thread, the input halo
-// staged in shared memory as BF16, warp-uniform weight loads), the same
-// kernel for the data gradient (with flipped, transposed weights), a weight
-// gradient kernel that reduces over a tile in registers then adds to global
-// FP32 with atomics, pooling/upsampling and their adjoints, the normalised
-// squared-error loss and Adam.
+// Convolutions run on the tensor cores (unet_tc.cuh: implicit GEMM with
+// mma.sync, BF16 operands, FP32 accumulation; activations and output
+// gradients are staged channel-last with the channel count padded to a
+// multiple of 8).  The data gradient is the forward kernel on the output
+// gradient (rounded to BF16) with flipped, transposed weights; the weight
+// gradient reduces per-CTA partials in a fixed order (no atomics), so a
+// gradient is bit-reproducible.  Pooling/upsampling and their adjoints, the
+// normalised squared-error loss and Adam are plain elementwise kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
 #include "internal.cuh"
 #include "ctx.cuh"
+#include "unet_tc.cuh"
 
 using stk::warp_sum;
 
@@ -31,144 +35,6 @@ namespace {
 struct Shape { int B, D, H, W; };
 __host__ __device__ inline int64_t vox(const Shape& s) { return (int64_t)s.B * s.D * s.H * s.W; }
 
-constexpr int CT_X = 8, CT_Y = 8, CT_Z3 = 4;     // 3D tile 8x8x4 = 256 voxels
-constexpr int CT2_X = 16, CT2_Y = 16;           // 2D tile 16x16
-
-__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
-__device__ __forceinline__ float to_f(float v) { return v; }
-template <class T> __device__ __forceinline__ T zero_of();
-template <> __device__ __forceinline__ __nv_bfloat16 zero_of<__nv_bfloat16>() { return __float2bfloat16(0.f); }
-template <> __device__ __forceinline__ float zero_of<float>() { return 0.f; }
-
-// ---- convolution (forward on BF16 activations; data gradient on FP32 ------
-// gradients with prepared weights)
-template <class TIN, int KZ, int COUT>
-__global__ void __launch_bounds__(256) k_conv(const TIN* __restrict__ X, Shape s, int cin,
-                                              const float* __restrict__ Wt, const float* __restrict__ bias,
-                                              int relu, __nv_bfloat16* __restrict__ Yb, float* __restrict__ Yf,
-                                              int ksize) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    TIN* sx = reinterpret_cast<TIN*>(smraw);
-    const int TXc = KZ == 3 ? CT_X : CT2_X, TYc = KZ == 3 ? CT_Y : CT2_Y, TZc = KZ == 3 ? CT_Z3 : 1;
-    const int R = ksize / 2;                 // halo radius (1 for 3x3, 0 for 1x1)
-    const int kz = KZ == 3 ? ksize : 1;
-    const int HX = TXc + 2 * R, HY = TYc + 2 * R, HZ = TZc + (KZ == 3 ? 2 * R : 0);
-    const int ntx = (s.W + TXc - 1) / TXc, nty = (s.H + TYc - 1) / TYc, ntz = (s.D + TZc - 1) / TZc;
-    int bid = blockIdx.x;
-    const int bx = bid % ntx; bid /= ntx;
-    const int by = bid % nty; bid /= nty;
-    const int bz = bid % ntz; const int b = bid / ntz;
-    const int x0 = bx * TXc, y0 = by * TYc, z0 = bz * TZc;
-    const int zr = KZ == 3 ? R : 0;
-    // stage the input halo
-    const int nh = HX * HY * HZ;
-    for (int e = threadIdx.x; e < nh * cin; e += 256) {
-        int c = e % cin, v = e / cin;
-        int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
-        int gx = x0 + hx - R, gy = y0 + hy - R, gz = z0 + hz - zr;
-        TIN val = zero_of<TIN>();
-        if (gx >= 0 && gx < s.W && gy >= 0 && gy < s.H && gz >= 0 && gz < s.D)
-            val = X[((((int64_t)b * s.D + gz) * s.H + gy) * s.W + gx) * cin + c];
-        sx[v * cin + c] = val;
-    }
-    __syncthreads();
-    const int tx = threadIdx.x % TXc, ty = (threadIdx.x / TXc) % TYc, tz = threadIdx.x / (TXc * TYc);
-    const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-    if (gx >= s.W || gy >= s.H || gz >= s.D) return;
-    float acc[COUT];
-#pragma unroll
-    for (int c = 0; c < COUT; ++c) acc[c] = bias ? bias[c] : 0.f;
-    int tap = 0;
-    for (int dz = 0; dz < kz; ++dz)
-        for (int dy = 0; dy < ksize; ++dy)
-            for (int dx = 0; dx < ksize; ++dx, ++tap) {
-                const TIN* xin = sx + (((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * cin;
-                const float* w = Wt + (int64_t)tap * cin * COUT;
-                for (int ci = 0; ci < cin; ++ci) {
-                    float v = to_f(xin[ci]);
-                    const float4* w4 = reinterpret_cast<const float4*>(w + ci * COUT);
-#pragma unroll
-                    for (int q = 0; q < COUT / 4; ++q) {
-                        float4 ww = __ldg(w4 + q);
-                        acc[4 * q] = fmaf(v, ww.x, acc[4 * q]);
-                        acc[4 * q + 1] = fmaf(v, ww.y, acc[4 * q + 1]);
-                        acc[4 * q + 2] = fmaf(v, ww.z, acc[4 * q + 2]);
-                        acc[4 * q + 3] = fmaf(v, ww.w, acc[4 * q + 3]);
-                    }
-                }
-            }
-    int64_t o = ((((int64_t)b * s.D + gz) * s.H + gy) * s.W + gx) * COUT;
-#pragma unroll
-    for (int c = 0; c < COUT; ++c) {
-        float v = relu ? fmaxf(acc[c], 0.f) : acc[c];
-        if (Yb) Yb[o + c] = __float2bfloat16(v);
-        if (Yf) Yf[o + c] = v;
-    }
-}
-
-// ---- weight gradient: dW[tap][ci][co] += sum_v X[v + tap][ci] dY[v][co] -----
-template <int KZ>
-__global__ void __launch_bounds__(256) k_conv_wgrad(const __nv_bfloat16* __restrict__ X, Shape s, int cin,
-                                                    const float* __restrict__ dY, int cout, int ksize,
-                                                    float* __restrict__ dW, float* __restrict__ db) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const int TXc = KZ == 3 ? CT_X : CT2_X, TYc = KZ == 3 ? CT_Y : CT2_Y, TZc = KZ == 3 ? CT_Z3 : 1;
-    const int R = ksize / 2, kz = KZ == 3 ? ksize : 1, zr = KZ == 3 ? R : 0;
-    const int HX = TXc + 2 * R, HY = TYc + 2 * R, HZ = TZc + 2 * zr;
-    float* sdy = reinterpret_cast<float*>(smraw);                               // 256 x cout
-    __nv_bfloat16* sx = reinterpret_cast<__nv_bfloat16*>(sdy + 256 * cout);     // halo x cin
-    const int ntx = (s.W + TXc - 1) / TXc, nty = (s.H + TYc - 1) / TYc, ntz = (s.D + TZc - 1) / TZc;
-    int bid = blockIdx.x;
-    const int bx = bid % ntx; bid /= ntx;
-    const int by = bid % nty; bid /= nty;
-    const int bz = bid % ntz; const int b = bid / ntz;
-    const int x0 = bx * TXc, y0 = by * TYc, z0 = bz * TZc;
-    const int nh = HX * HY * HZ;
-    for (int e = threadIdx.x; e < nh * cin; e += 256) {
-        int c = e % cin, v = e / cin;
-        int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
-        int gx = x0 + hx - R, gy = y0 + hy - R, gz = z0 + hz - zr;
-        __nv_bfloat16 val = __float2bfloat16(0.f);
-        if (gx >= 0 && gx < s.W && gy >= 0 && gy < s.H && gz >= 0 && gz < s.D)
-            val = X[((((int64_t)b * s.D + gz) * s.H + gy) * s.W + gx) * cin + c];
-        sx[v * cin + c] = val;
-    }
-    for (int e = threadIdx.x; e < 256 * cout; e += 256) {
-        int c = e % cout, v = e / cout;
-        int tx = v % TXc, ty = (v / TXc) % TYc, tz = v / (TXc * TYc);
-        int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-        float val = 0.f;
-        if (gx < s.W && gy < s.H && gz < s.D) val = dY[((((int64_t)b * s.D + gz) * s.H + gy) * s.W + gx) * cout + c];
-        sdy[e] = val;
-    }
-    __syncthreads();
-    const int taps = kz * ksize * ksize;
-    const int E = taps * cin * cout;
-    for (int e = threadIdx.x; e < E; e += 256) {
-        int co = e % cout, ci = (e / cout) % cin, tap = e / (cout * cin);
-        int dx = tap % ksize, dy = (tap / ksize) % ksize, dz = tap / (ksize * ksize);
-        float sum = 0.f;
-        for (int v = 0; v < 256; ++v) {
-            int tx = v % TXc, ty = (v / TXc) % TYc, tz = v / (TXc * TYc);
-            float xv = __bfloat162float(sx[(((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * cin + ci]);
-            sum = fmaf(xv, sdy[v * cout + co], sum);
-        }
-        atomicAdd(dW + e, sum);
-    }
-    if (threadIdx.x < cout) {
-        float sum = 0.f;
-        for (int v = 0; v < 256; ++v) sum += sdy[v * cout + threadIdx.x];
-        atomicAdd(db + threadIdx.x, sum);
-    }
-}
-
-// Data-gradient weights: W'[tap'][co][ci] = W[flip(tap')][ci][co]
-__global__ void k_flip_weights(const float* W, int taps, int cin, int cout, float* Wb) {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= taps * cin * cout) return;
-    int ci = e % cin, co = (e / cin) % cout, tp = e / (cin * cout);
-    Wb[e] = W[((int64_t)(taps - 1 - tp) * cin + ci) * cout + co];
-}
 
 // 2x average pooling (and its adjoint: nearest up-spread divided by 2^d)
 __global__ void k_pool(const __nv_bfloat16* X, Shape s, int c, int pz, __nv_bfloat16* Y) {
@@ -252,14 +118,13 @@ __global__ void k_relu_bwd(float* g, const __nv_bfloat16* y, int64_t n) {
     if (e < n && !(__bfloat162float(y[e]) > 0.f)) g[e] = 0.f;
 }
 
-__global__ void k_to_bf16(const float* x, __nv_bfloat16* y, int64_t n) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n) y[e] = __float2bfloat16(x[e]);
-}
-
-// loss = mean_b ||out_b - y_b||^2 / ||y_b||^2; g = d loss / d out
-__global__ void k_loss_sums(const float* out, const float* y, int64_t per, double* sums) {
-    int b = blockIdx.y;
+// loss = mean_b ||out_b - y_b||^2 / ||y_b||^2; g = d loss / d out.  The two
+// sums per sample are reduced deterministically: per-block partials (warp
+// shuffles, then warps in order), then the blocks in order.
+constexpr int LOSS_BLOCKS = 64;
+__global__ void k_loss_partials(const float* out, const float* y, int64_t per, double* part) {
+    __shared__ double red[2][8];
+    const int b = blockIdx.y;
     double num = 0.0, den = 0.0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < per; e += (int64_t)gridDim.x * blockDim.x) {
         float d = out[b * per + e] - y[b * per + e];
@@ -268,10 +133,24 @@ __global__ void k_loss_sums(const float* out, const float* y, int64_t per, doubl
     }
     num = warp_sum(num);
     den = warp_sum(den);
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(sums + 2 * b, num);
-        atomicAdd(sums + 2 * b + 1, den);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { red[0][w] = num; red[1][w] = den; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, c = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a += red[0][q]; c += red[1][q]; }
+        part[2 * (b * LOSS_BLOCKS + blockIdx.x)] = a;
+        part[2 * (b * LOSS_BLOCKS + blockIdx.x) + 1] = c;
     }
+}
+
+__global__ void k_loss_finish(const double* part, int B, double* sums) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double a = 0.0, c = 0.0;
+    for (int q = 0; q < LOSS_BLOCKS; ++q) { a += part[2 * (b * LOSS_BLOCKS + q)]; c += part[2 * (b * LOSS_BLOCKS + q) + 1]; }
+    sums[2 * b] = a;
+    sums[2 * b + 1] = c;
 }
 
 __global__ void k_loss_grad(const float* out, const float* y, int64_t per, int B, const double* sums, float* g) {
@@ -309,7 +188,15 @@ struct stokes_net_s {
     int64_t max_vox = 0;
     std::vector<Conv> L;
     int64_t np = 0;
-    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr, *wflip = nullptr;
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    // packed BF16 weights per layer: forward [cp(cout)][taps cp(cin)], data
+    // gradient [cp(cin)][taps cp(cout)]; the forward ones are repacked after
+    // every change of the parameters
+    std::vector<__nv_bfloat16*> wf, wg;
+    bool wf_valid = false;
+    __nv_bfloat16* g16 = nullptr;   // output gradient of the layer in BF16 (cp(cout) channels)
+    float* part = nullptr;          // weight-gradient partials, part_ctas x part_stride floats
+    int part_ctas = 0, sms = 0;
     int adam_t = 0;
     // activations (BF16) and gradients (FP32)
     __nv_bfloat16 *xin = nullptr, *e0a = nullptr, *e0 = nullptr, *p0 = nullptr, *e1a = nullptr, *e1 = nullptr,
@@ -325,69 +212,120 @@ struct stokes_net_s {
 
 namespace {
 
-int conv_cout_template_ok(int c) { return c == 4 || c == 8 || c == 12 || c == 16 || c == 24 || c == 32 || c == 48; }
+using unet_tc::cp8;
+// (cin, cout) the network supports: the tensor-core kernels are instantiated
+// for input channels padded to 8 or 16 and output channels padded to 8 or 16
+bool io_channels_ok(int c) { return c == 4 || c == 8 || c == 12 || c == 16; }
+constexpr int PART_STRIDE = 27 * 32 * 32 + 32;     // largest taps x cp(cin) x cp(cout) + cp(cout)
 
-template <int KZ, class TIN>
-cudaError_t conv_launch(stokes_net_s* n, const TIN* X, Shape s, int cin, const float* W, const float* b,
-                        int relu, __nv_bfloat16* Yb, float* Yf, int cout, int ks) {
-    const int TXc = KZ == 3 ? CT_X : CT2_X, TYc = KZ == 3 ? CT_Y : CT2_Y, TZc = KZ == 3 ? CT_Z3 : 1;
-    const int R = ks / 2;
-    size_t smem = (size_t)(TXc + 2 * R) * (TYc + 2 * R) * (TZc + (KZ == 3 ? 2 * R : 0)) * cin * sizeof(TIN);
-    unsigned grid = (unsigned)((int64_t)s.B * ((s.D + TZc - 1) / TZc) * ((s.H + TYc - 1) / TYc) * ((s.W + TXc - 1) / TXc));
-#define CASE(C)                                                                                             \
-    case C:                                                                                                 \
-        cudaFuncSetAttribute(k_conv<TIN, KZ, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
-        k_conv<TIN, KZ, C><<<grid, 256, smem, n->s>>>(X, s, cin, W, b, relu, Yb, Yf, ks);                   \
-        break;
-    switch (cout) {
-        CASE(4) CASE(8) CASE(12) CASE(16) CASE(24) CASE(32) CASE(48)
-        default: return cudaErrorInvalidValue;
-    }
-#undef CASE
+int taps_of(const stokes_net_s* n, const Conv& c) { return (n->KZ == 3 && c.ks == 3 ? 3 : 1) * c.ks * c.ks; }
+
+template <int KZ, int KS, int CP, int COUTP>
+cudaError_t launch_conv_tc(stokes_net_s* n, const __nv_bfloat16* X, Shape s, const __nv_bfloat16* Wp,
+                           const float* bias, int cout, int relu, __nv_bfloat16* Yb, float* Yf) {
+    using C = unet_tc::ConvCfg<KZ, KS, CP, COUTP>;
+    auto k = unet_tc::k_conv_tc<KZ, KS, CP, COUTP>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    const unet_tc::TShape ts{s.B, s.D, s.H, s.W};
+    k<<<C::G::tiles(ts), 256, C::SMEM, n->s>>>(X, ts, Wp, bias, cout, relu, Yb, Yf);
     return cudaGetLastError();
 }
 
-template <int KZ>
-cudaError_t wgrad_launch(stokes_net_s* n, const __nv_bfloat16* X, Shape s, int cin, const float* dY, int cout, int ks,
-                         float* dW, float* db) {
-    const int TXc = KZ == 3 ? CT_X : CT2_X, TYc = KZ == 3 ? CT_Y : CT2_Y, TZc = KZ == 3 ? CT_Z3 : 1;
-    const int R = ks / 2;
-    size_t smem = 256 * cout * 4 + (size_t)(TXc + 2 * R) * (TYc + 2 * R) * (TZc + (KZ == 3 ? 2 * R : 0)) * cin * 2;
-    unsigned grid = (unsigned)((int64_t)s.B * ((s.D + TZc - 1) / TZc) * ((s.H + TYc - 1) / TYc) * ((s.W + TXc - 1) / TXc));
-    cudaFuncSetAttribute(k_conv_wgrad<KZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_conv_wgrad<KZ><<<grid, 256, smem, n->s>>>(X, s, cin, dY, cout, ks, dW, db);
+// one convolution on the tensor cores: input X with cp channels, packed
+// weights Wp with coutp rows
+cudaError_t conv_tc(stokes_net_s* n, int ks, int cp, int coutp, const __nv_bfloat16* X, Shape s,
+                    const __nv_bfloat16* Wp, const float* bias, int cout, int relu, __nv_bfloat16* Yb, float* Yf) {
+#define CONV_CASE(KZ_, KS_, CP_, CO_)                                                                      \
+    if (n->KZ == KZ_ && ks == KS_ && cp == CP_ && coutp == CO_)                                            \
+        return launch_conv_tc<KZ_, KS_, CP_, CO_>(n, X, s, Wp, bias, cout, relu, Yb, Yf);
+#define CONV_CASES(KZ_)                                                                                    \
+    CONV_CASE(KZ_, 3, 8, 8) CONV_CASE(KZ_, 3, 16, 8) CONV_CASE(KZ_, 3, 8, 16) CONV_CASE(KZ_, 3, 16, 16)   \
+    CONV_CASE(KZ_, 3, 16, 32) CONV_CASE(KZ_, 3, 32, 32) CONV_CASE(KZ_, 3, 48, 16) CONV_CASE(KZ_, 3, 24, 8) \
+    CONV_CASE(KZ_, 3, 8, 24) CONV_CASE(KZ_, 3, 16, 48) CONV_CASE(KZ_, 3, 32, 16)                           \
+    CONV_CASE(KZ_, 1, 8, 8) CONV_CASE(KZ_, 1, 8, 16) CONV_CASE(KZ_, 1, 16, 8)
+    CONV_CASES(3)
+    CONV_CASES(1)
+#undef CONV_CASES
+#undef CONV_CASE
+    return cudaErrorInvalidValue;
+}
+
+template <int KZ, int KS, int CP, int COUTP>
+cudaError_t launch_wgrad_tc(stokes_net_s* n, const __nv_bfloat16* X, Shape s, const __nv_bfloat16* g16, int cin,
+                            int cout, float* dW, float* db) {
+    using C = unet_tc::WgCfg<KZ, KS, CP, COUTP>;
+    static_assert(C::E + COUTP <= PART_STRIDE, "partial buffer too small");
+    auto k = unet_tc::k_wgrad_tc<KZ, KS, CP, COUTP>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 256, (int)C::SMEM);
+    const unet_tc::TShape ts{s.B, s.D, s.H, s.W};
+    const int G = std::min({C::G::tiles(ts), n->sms * std::max(per, 1), n->part_ctas});
+    k<<<G, 256, C::SMEM, n->s>>>(X, ts, g16, n->part);
+    const int tot = C::E + COUTP;
+    unet_tc::k_wgrad_reduce<<<(tot + 255) / 256, 256, 0, n->s>>>(n->part, G, C::G::TAPS, CP, COUTP, cin, cout, dW,
+                                                                  db);
+    return cudaGetLastError();
+}
+
+cudaError_t wgrad_tc(stokes_net_s* n, int ks, int cp, int coutp, const __nv_bfloat16* X, Shape s,
+                     const __nv_bfloat16* g16, int cin, int cout, float* dW, float* db) {
+#define WG_CASE(KZ_, KS_, CP_, CO_)                                                                        \
+    if (n->KZ == KZ_ && ks == KS_ && cp == CP_ && coutp == CO_)                                            \
+        return launch_wgrad_tc<KZ_, KS_, CP_, CO_>(n, X, s, g16, cin, cout, dW, db);
+#define WG_CASES(KZ_)                                                                                      \
+    WG_CASE(KZ_, 3, 8, 8) WG_CASE(KZ_, 3, 16, 8) WG_CASE(KZ_, 3, 8, 16) WG_CASE(KZ_, 3, 16, 16)           \
+    WG_CASE(KZ_, 3, 16, 32) WG_CASE(KZ_, 3, 32, 32) WG_CASE(KZ_, 3, 48, 16) WG_CASE(KZ_, 3, 24, 8)         \
+    WG_CASE(KZ_, 1, 8, 8) WG_CASE(KZ_, 1, 8, 16)
+    WG_CASES(3)
+    WG_CASES(1)
+#undef WG_CASES
+#undef WG_CASE
+    return cudaErrorInvalidValue;
+}
+
+// pack the forward (and, for training, data-gradient) weights of every layer
+cudaError_t pack_weights(stokes_net_s* n, bool grad) {
+    for (size_t li = 0; li < n->L.size(); ++li) {
+        const Conv& c = n->L[li];
+        const int taps = taps_of(n, c);
+        if (!n->wf_valid) {
+            const int rows = cp8(c.cout), tot = rows * taps * cp8(c.cin);
+            unet_tc::k_pack_weights<<<nblk(tot), 256, 0, n->s>>>(n->theta + c.w_off, taps, c.cin, c.cout, rows,
+                                                                  cp8(c.cin), 0, n->wf[li]);
+        }
+        if (grad) {
+            const int rows = cp8(c.cin), tot = rows * taps * cp8(c.cout);
+            unet_tc::k_pack_weights<<<nblk(tot), 256, 0, n->s>>>(n->theta + c.w_off, taps, c.cin, c.cout, rows,
+                                                                  cp8(c.cout), 1, n->wg[li]);
+        }
+    }
+    n->wf_valid = true;
     return cudaGetLastError();
 }
 
 cudaError_t conv(stokes_net_s* n, int li, const __nv_bfloat16* X, Shape s, int relu, __nv_bfloat16* Yb, float* Yf) {
     const Conv& c = n->L[li];
-    if (n->KZ == 3)
-        return conv_launch<3, __nv_bfloat16>(n, X, s, c.cin, n->theta + c.w_off, n->theta + c.b_off, relu, Yb, Yf,
-                                             c.cout, c.ks);
-    return conv_launch<1, __nv_bfloat16>(n, X, s, c.cin, n->theta + c.w_off, n->theta + c.b_off, relu, Yb, Yf,
-                                         c.cout, c.ks);
+    return conv_tc(n, c.ks, cp8(c.cin), cp8(c.cout), X, s, n->wf[li], n->theta + c.b_off, c.cout, relu, Yb, Yf);
 }
 
-// data gradient of layer li: dX = conv(dY, flipped W) (no bias, no ReLU)
-cudaError_t conv_dgrad(stokes_net_s* n, int li, const float* dY, Shape s, float* dX) {
+// gradient step of layer li: dY (FP32, cout channels; the ReLU mask already
+// applied) -> BF16; weight and bias gradient from the layer input X; data
+// gradient into dX (FP32, cin channels) unless dX is null
+cudaError_t conv_backward(stokes_net_s* n, int li, const __nv_bfloat16* X, Shape s, const float* dY, float* dX) {
     const Conv& c = n->L[li];
-    int taps = (n->KZ == 3 ? c.ks : 1) * c.ks * c.ks;
-    k_flip_weights<<<nblk(c.nw), 256, 0, n->s>>>(n->theta + c.w_off, taps, c.cin, c.cout, n->wflip);
-    // gradients stay FP32 (staged as FP32 in shared memory)
-    if (n->KZ == 3) return conv_launch<3, float>(n, dY, s, c.cout, n->wflip, nullptr, 0, nullptr, dX, c.cin, c.ks);
-    return conv_launch<1, float>(n, dY, s, c.cout, n->wflip, nullptr, 0, nullptr, dX, c.cin, c.ks);
-}
-
-cudaError_t conv_wgrad(stokes_net_s* n, int li, const __nv_bfloat16* X, Shape s, const float* dY) {
-    const Conv& c = n->L[li];
-    if (n->KZ == 3) return wgrad_launch<3>(n, X, s, c.cin, dY, c.cout, c.ks, n->grad + c.w_off, n->grad + c.b_off);
-    return wgrad_launch<1>(n, X, s, c.cin, dY, c.cout, c.ks, n->grad + c.w_off, n->grad + c.b_off);
+    unet_tc::k_to_bf16_pad<<<nblk(vox(s) * cp8(c.cout)), 256, 0, n->s>>>(dY, vox(s), c.cout, cp8(c.cout), n->g16);
+    cudaError_t e = wgrad_tc(n, c.ks, cp8(c.cin), cp8(c.cout), X, s, n->g16, c.cin, c.cout, n->grad + c.w_off,
+                             n->grad + c.b_off);
+    if (e != cudaSuccess || !dX) return e;
+    return conv_tc(n, c.ks, cp8(c.cout), cp8(c.cin), n->g16, s, n->wg[li], nullptr, c.cin, 0, nullptr, dX);
 }
 
 Shape half(const Shape& s, int pz) { return Shape{s.B, pz ? s.D / 2 : s.D, s.H / 2, s.W / 2}; }
 
 cudaError_t forward(stokes_net_s* n, Shape s) {
     const int pz = n->KZ == 3;
+    if (!n->wf_valid && pack_weights(n, false) != cudaSuccess) return cudaGetLastError();
     Shape s1 = half(s, pz), s2 = half(s1, pz);
     cudaError_t e;
     if ((e = conv(n, 0, n->xin, s, 1, n->e0a, nullptr))) return e;
@@ -410,50 +348,41 @@ cudaError_t forward(stokes_net_s* n, Shape s) {
 // backward from dL/dout (in g_a), accumulating parameter gradients in grad
 cudaError_t backward(stokes_net_s* n, Shape s) {
     const int pz = n->KZ == 3;
+    if (pack_weights(n, true) != cudaSuccess) return cudaGetLastError();
     Shape s1 = half(s, pz), s2 = half(s1, pz);
     cudaError_t e;
     float *ga = n->g_a, *gb = n->g_b;
     auto relu_b = [&](float* g, const __nv_bfloat16* y, int64_t nel) { k_relu_bwd<<<nblk(nel), 256, 0, n->s>>>(g, y, nel); };
     // out (1x1, no ReLU): input d0
-    if ((e = conv_wgrad(n, 10, n->d0, s, ga))) return e;
-    if ((e = conv_dgrad(n, 10, ga, s, gb))) return e;                  // gb = d d0
+    if ((e = conv_backward(n, 10, n->d0, s, ga, gb))) return e;                  // gb = d d0
     relu_b(gb, n->d0, vox(s) * 8);
-    if ((e = conv_wgrad(n, 9, n->d0a, s, gb))) return e;
-    if ((e = conv_dgrad(n, 9, gb, s, ga))) return e;                   // ga = d d0a
+    if ((e = conv_backward(n, 9, n->d0a, s, gb, ga))) return e;                   // ga = d d0a
     relu_b(ga, n->d0a, vox(s) * 8);
-    if ((e = conv_wgrad(n, 8, n->c0, s, ga))) return e;
-    if ((e = conv_dgrad(n, 8, ga, s, gb))) return e;                   // gb = d c0 (24 ch)
+    if ((e = conv_backward(n, 8, n->c0, s, ga, gb))) return e;                   // gb = d c0 (24 ch)
     cudaMemsetAsync(n->g_skip0, 0, sizeof(float) * vox(s) * 8, n->s);
     k_up_concat_adj<<<nblk(std::max(vox(s1) * 16, vox(s) * 8)), 256, 0, n->s>>>(gb, s, 16, 8, pz, ga, n->g_skip0);
     // ga = d d1 (16 ch at s1)
     relu_b(ga, n->d1, vox(s1) * 16);
-    if ((e = conv_wgrad(n, 7, n->d1a, s1, ga))) return e;
-    if ((e = conv_dgrad(n, 7, ga, s1, gb))) return e;                  // gb = d d1a
+    if ((e = conv_backward(n, 7, n->d1a, s1, ga, gb))) return e;                  // gb = d d1a
     relu_b(gb, n->d1a, vox(s1) * 16);
-    if ((e = conv_wgrad(n, 6, n->c1, s1, gb))) return e;
-    if ((e = conv_dgrad(n, 6, gb, s1, ga))) return e;                  // ga = d c1 (48 ch at s1)
+    if ((e = conv_backward(n, 6, n->c1, s1, gb, ga))) return e;                  // ga = d c1 (48 ch at s1)
     cudaMemsetAsync(n->g_skip1, 0, sizeof(float) * vox(s1) * 16, n->s);
     k_up_concat_adj<<<nblk(std::max(vox(s2) * 32, vox(s1) * 16)), 256, 0, n->s>>>(ga, s1, 32, 16, pz, gb, n->g_skip1);
     // gb = d e2 (32 ch at s2)
     relu_b(gb, n->e2, vox(s2) * 32);
-    if ((e = conv_wgrad(n, 5, n->e2a, s2, gb))) return e;
-    if ((e = conv_dgrad(n, 5, gb, s2, ga))) return e;                  // ga = d e2a
+    if ((e = conv_backward(n, 5, n->e2a, s2, gb, ga))) return e;                  // ga = d e2a
     relu_b(ga, n->e2a, vox(s2) * 32);
-    if ((e = conv_wgrad(n, 4, n->p1, s2, ga))) return e;
-    if ((e = conv_dgrad(n, 4, ga, s2, gb))) return e;                  // gb = d p1 (16 ch at s2)
+    if ((e = conv_backward(n, 4, n->p1, s2, ga, gb))) return e;                  // gb = d p1 (16 ch at s2)
     k_pool_adj<<<nblk(vox(s1) * 16), 256, 0, n->s>>>(gb, s1, 16, pz, n->g_skip1);   // += into d e1
     relu_b(n->g_skip1, n->e1, vox(s1) * 16);
-    if ((e = conv_wgrad(n, 3, n->e1a, s1, n->g_skip1))) return e;
-    if ((e = conv_dgrad(n, 3, n->g_skip1, s1, ga))) return e;          // ga = d e1a
+    if ((e = conv_backward(n, 3, n->e1a, s1, n->g_skip1, ga))) return e;          // ga = d e1a
     relu_b(ga, n->e1a, vox(s1) * 16);
-    if ((e = conv_wgrad(n, 2, n->p0, s1, ga))) return e;
-    if ((e = conv_dgrad(n, 2, ga, s1, gb))) return e;                  // gb = d p0 (8 ch at s1)
+    if ((e = conv_backward(n, 2, n->p0, s1, ga, gb))) return e;                  // gb = d p0 (8 ch at s1)
     k_pool_adj<<<nblk(vox(s) * 8), 256, 0, n->s>>>(gb, s, 8, pz, n->g_skip0);      // += into d e0
     relu_b(n->g_skip0, n->e0, vox(s) * 8);
-    if ((e = conv_wgrad(n, 1, n->e0a, s, n->g_skip0))) return e;
-    if ((e = conv_dgrad(n, 1, n->g_skip0, s, ga))) return e;           // ga = d e0a
+    if ((e = conv_backward(n, 1, n->e0a, s, n->g_skip0, ga))) return e;           // ga = d e0a
     relu_b(ga, n->e0a, vox(s) * 8);
-    return conv_wgrad(n, 0, n->xin, s, ga);
+    return conv_backward(n, 0, n->xin, s, ga, nullptr);
 }
 
 }  // namespace
@@ -469,8 +398,7 @@ stokes_status stokes_net_destroy(stokes_net n) {
 }
 
 stokes_status stokes_net_create(stokes_net* out, int dim, int cin, int cout, int64_t max_voxels) {
-    if (!out || (dim != 2 && dim != 3) || cin < 1 || cin > 48 || !conv_cout_template_ok(cin) ||
-        !conv_cout_template_ok(cout) || max_voxels < 1)
+    if (!out || (dim != 2 && dim != 3) || !io_channels_ok(cin) || !io_channels_ok(cout) || max_voxels < 1)
         return STOKES_ERR_ARG;
     auto* n = new stokes_net_s();
     n->dim = dim; n->cin = cin; n->cout = cout; n->KZ = dim == 3 ? 3 : 1;
@@ -497,8 +425,20 @@ stokes_status stokes_net_create(stokes_net* out, int dim, int cin, int cout, int
     };
     int64_t V = max_voxels;
     A((void**)&n->theta, 4 * off); A((void**)&n->grad, 4 * off); A((void**)&n->m, 4 * off); A((void**)&n->v, 4 * off);
-    A((void**)&n->wflip, 4 * 27 * 48 * 48);
-    A((void**)&n->xin, 2 * V * cin);
+    for (const Conv& c : n->L) {
+        const int64_t taps = (dim == 3 && c.ks == 3 ? 3 : 1) * c.ks * c.ks;
+        n->wf.push_back(nullptr);
+        n->wg.push_back(nullptr);
+        A((void**)&n->wf.back(), 2 * taps * cp8(c.cin) * cp8(c.cout));
+        A((void**)&n->wg.back(), 2 * taps * cp8(c.cin) * cp8(c.cout));
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n->sms, cudaDevAttrMultiProcessorCount, dev);
+    n->part_ctas = 2 * std::max(n->sms, 1);
+    A((void**)&n->part, 4 * (size_t)n->part_ctas * PART_STRIDE);
+    A((void**)&n->g16, 2 * V * 8);
+    A((void**)&n->xin, 2 * V * cp8(cin));
     __nv_bfloat16** full8[] = {&n->e0a, &n->e0, &n->d0a, &n->d0};
     for (auto p : full8) A((void**)p, 2 * V * 8);
     A((void**)&n->c0, 2 * V * 24);
@@ -509,7 +449,7 @@ stokes_status stokes_net_create(stokes_net* out, int dim, int cin, int cout, int
     A((void**)&n->out, 4 * V * cout);
     A((void**)&n->g_a, 4 * V * 48); A((void**)&n->g_b, 4 * V * 48); A((void**)&n->g_c, 4 * V * 48);
     A((void**)&n->g_skip0, 4 * V * 8); A((void**)&n->g_skip1, 4 * V * 16);
-    A((void**)&n->sums, 16 * 1024);
+    A((void**)&n->sums, 16 * 1024 + 16 * 1024 * LOSS_BLOCKS);   // sums, then the per-block partials
     if (e != cudaSuccess) { stokes_net_destroy(n); return STOKES_ERR_CUDA; }
     *out = n;
     return STOKES_OK;
@@ -520,6 +460,7 @@ int64_t stokes_net_param_count(stokes_net n) { return n ? n->np : -1; }
 stokes_status stokes_net_set_params(stokes_net n, const float* host) {
     if (!n || !host) return STOKES_ERR_ARG;
     if (cudaMemcpy(n->theta, host, 4 * n->np, cudaMemcpyHostToDevice) != cudaSuccess) return STOKES_ERR_CUDA;
+    n->wf_valid = false;
     cudaMemset(n->m, 0, 4 * n->np);
     cudaMemset(n->v, 0, 4 * n->np);
     n->adam_t = 0;
@@ -541,7 +482,7 @@ static bool shape_ok(stokes_net n, int B, int D, int H, int W) {
 stokes_status stokes_net_forward(stokes_net n, int B, int D, int H, int W, const float* x, float* y) {
     if (!n || !x || !y || !shape_ok(n, B, D, H, W)) return STOKES_ERR_ARG;
     Shape s{B, D, H, W};
-    k_to_bf16<<<nblk(vox(s) * n->cin), 256, 0, n->s>>>(x, n->xin, vox(s) * n->cin);
+    unet_tc::k_to_bf16_pad<<<nblk(vox(s) * cp8(n->cin)), 256, 0, n->s>>>(x, vox(s), n->cin, cp8(n->cin), n->xin);
     if (forward(n, s) != cudaSuccess) return STOKES_ERR_CUDA;
     if (cudaMemcpyAsync(y, n->out, 4 * vox(s) * n->cout, cudaMemcpyDeviceToDevice, n->s) != cudaSuccess)
         return STOKES_ERR_CUDA;
@@ -554,11 +495,11 @@ stokes_status stokes_net_gradient(stokes_net n, int B, int D, int H, int W, cons
                                   double* loss, float* grad_host) {
     if (!n || !x || !y || !shape_ok(n, B, D, H, W) || B > 1024) return STOKES_ERR_ARG;
     Shape s{B, D, H, W};
-    k_to_bf16<<<nblk(vox(s) * n->cin), 256, 0, n->s>>>(x, n->xin, vox(s) * n->cin);
+    unet_tc::k_to_bf16_pad<<<nblk(vox(s) * cp8(n->cin)), 256, 0, n->s>>>(x, vox(s), n->cin, cp8(n->cin), n->xin);
     if (forward(n, s) != cudaSuccess) return STOKES_ERR_CUDA;
     int64_t per = (int64_t)D * H * W * n->cout;
-    cudaMemsetAsync(n->sums, 0, 16 * B, n->s);
-    k_loss_sums<<<dim3(64, B), 256, 0, n->s>>>(n->out, y, per, n->sums);
+    k_loss_partials<<<dim3(LOSS_BLOCKS, B), 256, 0, n->s>>>(n->out, y, per, n->sums + 2 * 1024);
+    k_loss_finish<<<(B + 127) / 128, 128, 0, n->s>>>(n->sums + 2 * 1024, B, n->sums);
     k_loss_grad<<<nblk(per * B), 256, 0, n->s>>>(n->out, y, per, B, n->sums, n->g_a);
     cudaMemsetAsync(n->grad, 0, 4 * n->np, n->s);
     if (backward(n, s) != cudaSuccess) return STOKES_ERR_CUDA;
@@ -583,6 +524,7 @@ stokes_status stokes_net_train_step(stokes_net n, int B, int D, int H, int W, co
     const float b1 = 0.9f, b2 = 0.999f;
     float c1 = 1.f - std::pow(b1, (float)n->adam_t), c2 = 1.f - std::pow(b2, (float)n->adam_t);
     k_adam<<<nblk(n->np), 256, 0, n->s>>>(n->theta, n->grad, n->m, n->v, n->np, lr, b1, b2, 1e-8f, c1, c2);
+    n->wf_valid = false;
     return cudaStreamSynchronize(n->s) == cudaSuccess ? STOKES_OK : STOKES_ERR_CUDA;
 }
 

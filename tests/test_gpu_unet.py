@@ -1,13 +1,18 @@
 """The CUDA U-Net against the FP64 CPU reference (oracle.unet).
 
-BF16 activations with FP32 accumulation.  Against the FP64 reference that
-stores its activations in BF16 the same way (oracle.unet.bf16_store, so both
-sides take the same ReLU decisions) the forward output must agree to 2e-3
-relative (RMS over the output) and the parameter gradient to a cosine
-similarity >= 0.9999 and a relative norm difference <= 1e-2.  Against the
-plain FP64 network the forward output must agree to 2e-2 and the gradient to
-a cosine >= 0.995 (the rest is the BF16 storage itself).  A few Adam steps
-must reduce the loss."""
+The convolutions run on the tensor cores with BF16 operands (activations,
+weights and, in the backward pass, the gradients at each convolution's
+output) and FP32 accumulation.  Against the FP64 reference evaluated at the
+values the kernels store -- BF16-rounded weights and BF16 activations
+(oracle.unet.bf16_store, so both sides take the same ReLU decisions) -- the
+forward output must agree to 2e-3 relative (RMS over the output) and the
+parameter gradient to a cosine similarity >= 0.9999 and a relative norm
+difference <= 1e-2 (measured: 0.999996, 3e-4).  Against the plain FP64
+network the forward output must agree to 2e-2 and the gradient to a cosine
+>= 0.985 (measured 0.9907 in 2D: the rest is the BF16 storage of weights,
+activations and output gradients).  A gradient is bit-reproducible (the weight gradient sums
+per-CTA partials in a fixed order).  A few Adam steps must reduce the
+loss."""
 import numpy as np
 import pytest
 
@@ -16,6 +21,18 @@ from oracle import unet as U
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
+
+
+def _bf16_weights(theta, dim, cin, cout):
+    """The oracle-layout parameters with every weight (not the biases)
+    rounded to BF16, as the kernels hold them."""
+    out = np.array(theta, dtype=np.float64)
+    o = 0
+    for _, co, ci, k in U.layer_shapes(dim, cin, cout):
+        nw = co * ci * int(np.prod(k))
+        out[o:o + nw] = torch.tensor(out[o:o + nw]).to(torch.bfloat16).to(torch.float64).numpy()
+        o += nw + co
+    return out
 
 
 def _setup(dim, cin, cout, shape, seed):
@@ -45,7 +62,8 @@ def test_forward_matches_oracle(dim, cin, cout, shape):
     got = net.forward(torch.tensor(x.reshape(-1)).cuda(), shape).cpu().numpy().reshape(y.shape)
     got = np.moveaxis(got, -1, 1)
     for store, tol in ((U.bf16_store, 2e-3), (None, 2e-2)):
-        ref = U.predict(th32, to_nc(xb), dim, cin, cout, store=store)
+        th_ref = _bf16_weights(th32, dim, cin, cout) if store else th32
+        ref = U.predict(th_ref, to_nc(xb), dim, cin, cout, store=store)
         err = np.sqrt(np.mean((got - ref) ** 2)) / np.sqrt(np.mean(ref ** 2))
         assert err < tol, (store, err)
 
@@ -58,8 +76,11 @@ def test_gradient_matches_oracle(dim, cin, cout, shape):
     theta = net.to_oracle_layout(net.get_params())
     L, g = net.gradient(torch.tensor(x.reshape(-1)).cuda(), torch.tensor(y.reshape(-1)).cuda(), shape)
     g = net.to_oracle_layout(g)
-    for store, ltol, ctol, ntol in ((U.bf16_store, 2e-3, 0.9999, 1e-2), (None, 2e-2, 0.995, 5e-2)):
-        L_ref, g_ref = U.loss_and_grad(theta, to_nc(xb), to_nc(y), dim, cin, cout, store=store)
+    L2, g2 = net.gradient(torch.tensor(x.reshape(-1)).cuda(), torch.tensor(y.reshape(-1)).cuda(), shape)
+    assert L2 == L and np.array_equal(net.to_oracle_layout(g2), g)
+    for store, ltol, ctol, ntol in ((U.bf16_store, 2e-3, 0.9999, 1e-2), (None, 2e-2, 0.985, 5e-2)):
+        th_ref = _bf16_weights(theta, dim, cin, cout) if store else theta
+        L_ref, g_ref = U.loss_and_grad(th_ref, to_nc(xb), to_nc(y), dim, cin, cout, store=store)
         assert abs(L - L_ref) <= ltol * abs(L_ref), (store, L, L_ref)
         cos = g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref))
         assert cos >= ctol, (store, cos)
