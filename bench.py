@@ -121,6 +121,11 @@ WORKLOADS = {
     "batch64": dict(desc="64 independent 2D instances, n ~ U{64..512}, Gaussian-bump liquid, random moving disk, "
                          "mu log-uniform 1e-2..1e2, rho=1, each to 1e-8, one persistent launch under a CUDA graph",
                     dim=2),
+    "learned128": dict(desc="3D Gaussian-bump instances (8 bumps, moving sphere, log-uniform mu 1e-2..1e2, rho 1|1000): "
+                            "BF16 3-level U-Net (tensor cores) trained on 2,000 solver-generated residual/error pairs "
+                            "(64^3 windows of 128^3 instances), then held-out 128^3 and 256^3 instances solved to 1e-8 "
+                            "by the learned flexible CG, by Jacobi-CG in the same mixed precision and by plain FP64 "
+                            "Jacobi-PCG", dim=3),
     "jet150": dict(desc="the planar viscous jet at 150^2 (circle container r=0.4, inflow D=0.06 at U=-0.5, "
                         "mu=0.075, rho=1, g=-9.81, dt=0.002): one Navier-Stokes step = transport + weight build "
                         "+ Schwarz setup + Stokes step to 1e-8", dim=2),
@@ -199,6 +204,27 @@ def run_batched(args, rank, world):
         "one_by_one": {"ms_sum": seq_ms, "iterations_max": max(seq_iters),
                        "note": "same instances solved one after another, FP64 Jacobi-PCG each in its own graph"},
         "clocks": clk.summary(),
+    }
+
+
+def run_learned(args, rank, world):
+    """The learned preconditioner at the stated scale (one run, not a timed
+    loop: the training itself is the work; value = device time of the
+    learned solve on the first held-out 128^3 instance)."""
+    import torch
+    from paper_1010_2832_gb300 import learned
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    with ClockSampler(dev.index) as clk:
+        res = learned.config5(log=lambda m: print(m, file=sys.stderr, flush=True))
+    first = res["eval"][0]
+    return {
+        "metric": "time-to-solution per implicit step at 1e-8 rel. residual", "value": first["learned"]["ms_device"],
+        "unit": "ms", "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": first["learned"]["ms_device"],
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 network (f32 accumulation), f32 flexible CG inside f64 refinement", "data": "synthetic (seeded)",
+        "config": {"workload": "learned128", "desc": WORKLOADS["learned128"]["desc"], "parallelism": f"replicas x{world}"},
+        "learned": res, "clocks": clk.summary(),
     }
 
 
@@ -829,8 +855,8 @@ def main():
     if world > 1:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
-    if args.workload in ("batch64", "jet150"):
-        out = (run_batched if args.workload == "batch64" else run_jet)(args, rank, world)
+    if args.workload in ("batch64", "jet150", "learned128"):
+        out = {"batch64": run_batched, "jet150": run_jet, "learned128": run_learned}[args.workload](args, rank, world)
         if rank == 0:
             print(json.dumps(out))
         if world > 1:

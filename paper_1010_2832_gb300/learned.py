@@ -118,3 +118,123 @@ def _field_sizes(ctx):
     nz = ctx.n[2]
     return [nx * ny * nz, nx * ny * nz, nz * (ny + 1) * (nx + 1), (nz + 1) * ny * (nx + 1),
             (nz + 1) * (ny + 1) * nx, nx * ny * nz]
+
+
+def crop(t, grid, channels, corner, size):
+    """A size^3 (3D) or size^2 (2D) window of a flat channel-last tensor on
+    the network grid (D, H, W), starting at corner (z, y, x)."""
+    D, H, W = grid
+    v = t.view(D, H, W, channels)
+    z, y, x = corner
+    if D == 1:
+        return v[:, y:y + size, x:x + size, :].contiguous().view(-1)
+    return v[z:z + size, y:y + size, x:x + size, :].contiguous().view(-1)
+
+
+def make_cropped_pairs(ctx, wl, n_pairs, seed0, size, cg_iters=(0, 4, 16, 64, 256)):
+    """The pairs of make_pairs (pair q: white-noise or smooth start as q is
+    even or odd, cg_iters[q % len] Jacobi-PCG iterations), each cut to a
+    seeded random window of the given size (corner on a multiple of 4, so
+    the network's pooling grid is the one it has on the whole grid); only
+    the windows are kept."""
+    D, H, W, cin, cout = stokes.learned_grid(ctx)
+    rng = np.random.default_rng(seed0)
+    lim = [(d - size) // 4 for d in (D, H, W)]
+    out = []
+    b = ctx.new_vector()
+    x = ctx.new_vector()
+    r = ctx.new_vector()
+    z32 = ctx.new_vector(torch.float32)
+    for q in range(n_pairs):
+        e0 = white_error(ctx, seed0 + q) if q % 2 == 0 else smooth_error(ctx, wl, seed0 + q)
+        k = cg_iters[q % len(cg_iters)]
+        e = e0
+        if k > 0:
+            ctx.apply(e0, b, stokes.FP64)
+            x.zero_()
+            ctx.solve_system(b, x, stokes.default_options(mode=stokes.FP64, precond=0, tol=1e-300, max_iter=k))
+            e = e0 - x
+        ctx.apply(e, r, stokes.FP64)
+        feats, rms = stokes.learned_features(ctx, r)
+        ctx.apply_preconditioner(0, r.float(), z32)
+        targ = stokes.learned_targets(ctx, e - z32.double(), rms)
+        corner = tuple(4 * int(rng.integers(0, m + 1)) if m > 0 else 0 for m in lim)
+        out.append((crop(feats, (D, H, W), cin, corner, size), crop(targ, (D, H, W), cout, corner, size)))
+        del feats, targ
+    return out
+
+
+def compare_solvers(ctx, dev, net, max_iter=400000):
+    """The learned flexible CG (mixed precision), the same solve with Jacobi
+    alone, and plain FP64 Jacobi-PCG on one system: status, iterations,
+    device and wall time, final true residual."""
+    row = {}
+    for name, mode, prec in (("learned", stokes.FP32, 1), ("jacobi_fp32", stokes.FP32, 0),
+                             ("plain_fp64", stokes.FP64, 0)):
+        if prec == 1:
+            stokes.attach_network(ctx, net)
+        st, ms, _ = solve(ctx, dev, mode=mode, precond=prec, max_iter=max_iter)
+        row[name] = dict(status=st["status"], iterations=st["iterations"], ms_device=st["ms_solve"], ms_wall=ms,
+                         rel_residual=st["rel_residual"],
+                         jacobi_fallback_steps=stokes.learned_jacobi_steps(ctx) if prec == 1 else 0)
+    return row
+
+
+def init_network(net, seed=0):
+    """He-uniform weights (limit sqrt(6 / fan_in)), zero biases, in the
+    library's parameter layout."""
+    rng = np.random.default_rng(seed)
+    p = np.zeros(net.n, dtype=np.float32)
+    for ci, co, ks, wo, bo in net.layers():
+        taps = ks ** net.dim
+        lim = np.sqrt(6.0 / (ci * taps))
+        p[wo:wo + taps * ci * co] = rng.uniform(-lim, lim, taps * ci * co)
+    net.set_params(p)
+
+
+def config5(n_train=128, instances=40, pairs_per_instance=50, crop_size=64, epochs=30, batch=4, lr=2e-3,
+            eval_sizes=(128, 128, 256), eval_seed0=9000, train_seed0=5000, max_iter=400000, log=None):
+    """The learned preconditioner at scale: solver-generated pairs from 3D
+    Gaussian-bump instances (seeds train_seed0..), cut to crop_size^3
+    windows, train the BF16 U-Net on the tensor cores, then solve held-out
+    instances (seeds eval_seed0.., sizes eval_sizes) with the learned
+    flexible CG, the same mixed-precision CG with Jacobi alone, and plain
+    FP64 Jacobi-PCG.  Returns a dict of timings, losses and per-instance
+    comparisons."""
+    from . import workloads as W
+    say = log or (lambda *a: None)
+    t0 = time.perf_counter()
+    data = []
+    cin = cout = None
+    for i in range(instances):
+        wl = W.bumps_3d(n_train, seed=train_seed0 + i)
+        ctx, dev = stokes.context_for(wl)
+        D, H, Wd, cin, cout = stokes.learned_grid(ctx)
+        data += make_cropped_pairs(ctx, wl, pairs_per_instance, seed0=100000 * (i + 1), size=crop_size)
+        ctx.close()
+        del dev
+        torch.cuda.empty_cache()
+    t_data = time.perf_counter() - t0
+    say(f"pairs: {len(data)} in {t_data:.1f} s")
+    eval_grids = [(s + 4) // 4 * 4 for s in eval_sizes]
+    max_vox = max([batch * crop_size ** 3] + [g ** 3 for g in eval_grids])
+    net = stokes.Net(3, cin, cout, max_vox)
+    init_network(net, seed=3)
+    t0 = time.perf_counter()
+    losses = train(net, data, (crop_size,) * 3, epochs=epochs, batch=batch, lr=lr, log=say)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del data
+    torch.cuda.empty_cache()
+    rows = []
+    for k, size in enumerate(eval_sizes):
+        wl = W.bumps_3d(size, seed=eval_seed0 + k)
+        ctx, dev = stokes.context_for(wl)
+        row = dict(n=size, seed=eval_seed0 + k, **compare_solvers(ctx, dev, net, max_iter=max_iter))
+        say(f"eval {size}^3: {row}")
+        rows.append(row)
+        ctx.close()
+        del dev
+        torch.cuda.empty_cache()
+    return dict(pairs=instances * pairs_per_instance, crop=crop_size, instances=instances, n_train=n_train,
+                params=int(net.n), epochs=epochs, train_loss=losses, s_pairs=t_data, s_train=t_train, eval=rows)
