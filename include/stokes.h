@@ -374,7 +374,9 @@ stokes_status stokes_solve_batched(int n, const stokes_ctx* ctxs, const stokes_b
  * are BF16, accumulation and master weights FP32.  Tensors passed in are FP32
  * device arrays, channel-last (B, D, H, W, C) with D = 1 in 2D, H and W
  * multiples of 4 (D too in 3D); ``cin`` and ``cout`` must be one of 4, 8,
- * 12, 16, 24, 32, 48.  The flat parameter vector holds, per convolution in
+ * 12, 16.  The convolutions run on the tensor cores with BF16 operands
+ * (activations, weights, and output gradients in the backward pass) and
+ * FP32 accumulation; a gradient is bit-reproducible.  The flat parameter vector holds, per convolution in
  * the order enc0a enc0b enc1a enc1b enc2a enc2b dec1a dec1b dec0a dec0b out,
  * the weights W[tap][cin][cout] then the bias (stokes_net_layer gives the
  * offsets).  All calls run on the network's own stream and synchronise.
