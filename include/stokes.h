@@ -443,8 +443,8 @@ double stokes_schwarz_setup_ms(stokes_ctx ctx);
  * reserved up front by its own pool, or a real-time loop that cannot accept
  * the device-wide synchronisation of cudaMalloc/cudaFree).  Same arguments,
  * layout and result; it allocates nothing, host or device: its scratch is a
- * fixed 8 MiB device array inside the library, which bounds the grid to about
- * 540^2 (larger grids: STOKES_ERR_ARG with the sizes in stokes_last_error).
+ * fixed 8 MiB device array inside the library, which bounds 2D grids to
+ * 555^2 (larger grids: STOKES_ERR_ARG with the sizes in stokes_last_error).
  * The context's Schwarz plan must already exist (an earlier
  * stokes_apply_preconditioner(ctx, 2, ...) or a solve with precond = 2 after
  * the last weight build), else STOKES_ERR_STATE.  The context's device must

@@ -774,7 +774,7 @@ cudaError_t schwarz_ensure(Ctx* c, const SchwarzPlan** plan) {
 // synchronises the context's stream.  Every call uses the same array: calls
 // that overlap on the GPU (other streams, other contexts, other threads) race
 // and give wrong results.
-constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(8) << 20;   // 8 MiB: 2D grids up to about 540^2
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(8) << 20;   // 8 MiB: 2D grids up to 555^2
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 constexpr int NOALLOC_MAX_DEVICES = 64;
 static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES];
@@ -808,7 +808,7 @@ cudaError_t apply_schwarz_noalloc(Ctx* c, const float* r, float* z, std::string*
     if (lo.total > NOALLOC_SCRATCH_BYTES) {
         *why = "grid too large for the allocation-free scratch: needs " + std::to_string(lo.total) +
                " bytes, the fixed maximum is " + std::to_string(NOALLOC_SCRATCH_BYTES) +
-               " (2D grids up to about 540^2); use stokes_apply_preconditioner";
+               " (2D grids up to 555^2); use stokes_apply_preconditioner";
         return cudaErrorInvalidValue;
     }
     int dev = 0;
