@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
     const int n8 = (n + 7) / 8 * 8;
     for (int e = t; e < n * n8; e += 256) {
         const int r = e / n8, c = e % n8;
-        if (c < (r / 8 + 1) * 8) Xh[tri8_off(r) + c] = __float2half_rn(c <= r ? X[r * PMAX + c] * rho_inv[r] : 0.f);
+        if (c < (r / 8 + 1) * 8) Xh[sw_fac_off(r, c, n)] = __float2half_rn(c <= r ? X[r * PMAX + c] * rho_inv[r] : 0.f);
     }
     for (int e = t; e < PMAX; e += 256) P.scale[(int64_t)p * PMAX + e] = map[e] >= 0 ? sc[map[e]] : 0.f;
 }

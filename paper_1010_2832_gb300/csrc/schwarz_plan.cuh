@@ -17,10 +17,19 @@ constexpr int PMAX8 = (PMAX + 7) / 8 * 8;   // local vectors padded to blocks of
 // each row r scaled by rho_r = max_c |X[r][c]|, kept as FP16 (X~ = X / rho_r
 // in [-1, 1]) with rho_r^2 in FP32; the operator is X~^T diag(rho^2) X~.
 // Layout: PMAX FP32 row factors rho_r^2 (432 bytes), then the packed lower
-// triangle of X~ with every row padded to a multiple of 8 entries, so rows
-// start on 16-byte boundaries: row r (group m = r / 8, rows of group m hold
-// 8(m+1) entries) starts at 32 m (m+1) + (r - 8m) 8 (m+1) halves.
+// triangle of X~ by bands of 8 rows: band m (rows 8m .. 8m+7, of which an
+// n-row patch keeps k = min(8, n - 8m)) holds 8(m+1) columns, stored as
+// m + 1 blocks of 8 columns, each block with the band's k rows one after
+// another (16 bytes per row).  The 8 rows of an 8 x 8 block are then one
+// contiguous 128-byte run, which ldmatrix reads without bank conflicts.
+// Band m starts at 32 m (m+1) halves; tri8_off(r) is where row r would end
+// the stored triangle (the first r rows take tri8_off(r) halves).
 __host__ __device__ constexpr int tri8_off(int r) { return 32 * (r / 8) * (r / 8 + 1) + (r - 8 * (r / 8)) * 8 * (r / 8 + 1); }
+// Offset (halves) of entry (r, c), c < 8 (r / 8 + 1), in an n-row patch.
+__host__ __device__ constexpr int sw_fac_off(int r, int c, int n) {
+    return 32 * (r / 8) * (r / 8 + 1) + (c / 8) * 8 * (n - 8 * (r / 8) < 8 ? n - 8 * (r / 8) : 8) + (r % 8) * 8 +
+           c % 8;
+}
 constexpr int SW_RS_BYTES = PMAX * (int)sizeof(float);                       // 432
 constexpr int SW_FAC_BYTES = SW_RS_BYTES + tri8_off(PMAX) * 2;               // 12,976 bytes per patch
 // Bytes of a patch's stored factor with n unknowns (a multiple of 16).
@@ -219,8 +228,12 @@ __device__ __forceinline__ void sw_factor_products(const uint8_t* F, int n, floa
         int rowA = 16 * mA + (li & 1) * 8 + lj, rowB = 16 * max(mB, 0) + (li & 1) * 8 + lj;
         rowA = rowA < n ? rowA : 0;
         rowB = rowB < n ? rowB : 0;
-        const uint32_t baseA = X + 2u * (uint32_t)(tri8_off(rowA) + (li >> 1) * 8);
-        const uint32_t baseB = X + 2u * (uint32_t)(tri8_off(rowB) + (li >> 1) * 8);
+        // column block (li >> 1) of the first k-tile; the next k-tile is two
+        // blocks (16 k halves, k = rows kept in the row's band) further on
+        const uint32_t baseA = X + 2u * (uint32_t)sw_fac_off(rowA, (li >> 1) * 8, n);
+        const uint32_t baseB = X + 2u * (uint32_t)sw_fac_off(rowB, (li >> 1) * 8, n);
+        const uint32_t stepA = 32u * (uint32_t)min(8, n - 8 * (rowA / 8));
+        const uint32_t stepB = 32u * (uint32_t)min(8, n - 8 * (rowB / 8));
         const bool onA = mA < ntile, onB = mB >= 0 && mB < ntile;
 #pragma unroll
         for (int kt = 0; kt < 7; ++kt) {
@@ -229,13 +242,13 @@ __device__ __forceinline__ void sw_factor_products(const uint8_t* F, int n, floa
             sw_b_frag(hb, kt, lane, b0, b1);
             if (onA && kt <= mA) {
                 uint32_t a[4];
-                ldsm_x4(a, baseA + 32u * kt);
+                ldsm_x4(a, baseA + stepA * kt);
                 if (kt == mA) a[2] = 0u;                 // upper 8 x 8 block of the diagonal tile
                 mma_f16_16816(dA, a, b0, b1);
             }
             if (onB && kt <= mB) {
                 uint32_t a[4];
-                ldsm_x4(a, baseB + 32u * kt);
+                ldsm_x4(a, baseB + stepB * kt);
                 if (kt == mB) a[2] = 0u;
                 mma_f16_16816(dB, a, b0, b1);
             }
@@ -269,16 +282,15 @@ __device__ __forceinline__ void sw_factor_products(const uint8_t* F, int n, floa
             sw_b_frag(hb, rt, lane, b0, b1);
             int row = 16 * rt + (li >> 1) * 8 + lj;
             row = row < n ? row : 0;
-            const uint32_t rb = X + 2u * (uint32_t)tri8_off(row);
             if (onA && rt >= cA) {
                 uint32_t a[4];
-                ldsm_x4_trans(a, rb + 2u * cofsA);
+                ldsm_x4_trans(a, X + 2u * (uint32_t)sw_fac_off(row, cofsA, n));
                 if (rt == cA) a[1] = 0u;                 // upper 8 x 8 block of the diagonal tile
                 mma_f16_16816(dA, a, b0, b1);
             }
             if (onB && rt >= cB) {
                 uint32_t a[4];
-                ldsm_x4_trans(a, rb + 2u * cofsB);
+                ldsm_x4_trans(a, X + 2u * (uint32_t)sw_fac_off(row, cofsB, n));
                 if (rt == cB) a[1] = 0u;
                 mma_f16_16816(dB, a, b0, b1);
             }
