@@ -15,7 +15,9 @@
   wall only touches inactive unknowns).  The GPU solves the full grid; the
   oracle builds the window system, and the GPU's fractions, activity and
   solution are checked there (fractions to 1e-12: the window's lattice
-  coordinates round differently from the full grid's)."""
+  coordinates round differently from the full grid's), and the velocities
+  at 4,096 stored faces of the oracle's solve of the window within 1e-6 of
+  max |u|."""
 import numpy as np
 import pytest
 
@@ -97,3 +99,9 @@ def test_column256_on_its_liquid_window():
         parts.append(t.cpu().numpy().reshape(G.field_shape(kd, n, n, n))[_window_slices(kd, win)].ravel())
     xw = np.concatenate(parts)
     assert So.relative_residual(S.A, xw, S.b) <= 1.01e-8
+    # velocities against the oracle's solve of the window (stored at 4,096
+    # seeded faces), indices mapped from the window's faces to the grid's
+    import bench
+    idx, val, scale = golden_velocity_samples("column256")
+    uu = torch.cat([a.reshape(-1) for a in u]).cpu().numpy()
+    assert np.abs(uu[bench.window_face_to_full(idx, n, win)] - val).max() <= 1e-6 * scale
