@@ -121,11 +121,11 @@ WORKLOADS = {
     "batch64": dict(desc="64 independent 2D instances, n ~ U{64..512}, Gaussian-bump liquid, random moving disk, "
                          "mu log-uniform 1e-2..1e2, rho=1, each to 1e-8, one persistent launch under a CUDA graph",
                     dim=2),
-    "learned128": dict(desc="3D Gaussian-bump instances (8 bumps, moving sphere, log-uniform mu 1e-2..1e2, rho 1|1000): "
-                            "BF16 3-level U-Net (tensor cores) trained on 2,000 solver-generated residual/error pairs "
-                            "(64^3 windows of 128^3 instances), then held-out 128^3 and 256^3 instances solved to 1e-8 "
-                            "by the learned flexible CG, by Jacobi-CG in the same mixed precision and by plain FP64 "
-                            "Jacobi-PCG", dim=3),
+    "learned128": dict(desc="3D Gaussian-bump instances (8 bumps, moving sphere, log-uniform mu 1e-2..1e2, rho 1|1000; "
+                            "face-mass floor 0.01): BF16 3-level U-Net (tensor cores) trained on 2,000 solver-generated "
+                            "residual/error pairs (64^3 windows of 20 128^3 instances), then held-out 128^3 and 256^3 "
+                            "instances solved to 1e-8 by the learned flexible CG, by Jacobi-CG in the same mixed "
+                            "precision and by plain FP64 Jacobi-PCG", dim=3),
     "jet150": dict(desc="the planar viscous jet at 150^2 (circle container r=0.4, inflow D=0.06 at U=-0.5, "
                         "mu=0.075, rho=1, g=-9.81, dt=0.002): one Navier-Stokes step = transport + weight build "
                         "+ Schwarz setup + Stokes step to 1e-8", dim=2),

@@ -391,8 +391,9 @@ stokes_status stokes_net_layer(stokes_net net, int i, int* cin, int* cout, int* 
 stokes_status stokes_net_set_params(stokes_net net, const float* host_params);
 stokes_status stokes_net_get_params(stokes_net net, float* host_params);
 stokes_status stokes_net_forward(stokes_net net, int B, int D, int H, int W, const float* x, float* y);
-/* loss = mean over the batch of ||N(x_b) - y_b||^2 / ||y_b||^2, and its
- * gradient with respect to the parameters (copied to grad_host if given). */
+/* loss = mean over the batch of ||N(x_b) - y_b||^2 / ||y_b||^2 (a sample with
+ * y_b = 0 contributes 0), and its gradient with respect to the parameters
+ * (copied to grad_host if given). */
 stokes_status stokes_net_gradient(stokes_net net, int B, int D, int H, int W, const float* x, const float* y,
                                   double* loss, float* grad_host);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on that loss. */

@@ -157,7 +157,9 @@ __global__ void k_loss_grad(const float* out, const float* y, int64_t per, int B
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= per * B) return;
     int b = e / per;
-    double den = fmax(sums[2 * b + 1], 1e-300);
+    // a sample whose target is zero contributes nothing (no gradient)
+    if (!(sums[2 * b + 1] > 0.0)) { g[e] = 0.f; return; }
+    double den = sums[2 * b + 1];
     g[e] = (float)(2.0 * (out[e] - y[e]) / den / B);
 }
 
@@ -508,7 +510,7 @@ stokes_status stokes_net_gradient(stokes_net n, int B, int D, int H, int W, cons
     if (cudaStreamSynchronize(n->s) != cudaSuccess) return STOKES_ERR_CUDA;
     if (loss) {
         double L = 0;
-        for (int b = 0; b < B; ++b) L += sums[2 * b] / std::fmax(sums[2 * b + 1], 1e-300);
+        for (int b = 0; b < B; ++b) L += sums[2 * b + 1] > 0.0 ? sums[2 * b] / sums[2 * b + 1] : 0.0;
         *loss = L / B;
     }
     if (grad_host && cudaMemcpy(grad_host, n->grad, 4 * n->np, cudaMemcpyDeviceToHost) != cudaSuccess)

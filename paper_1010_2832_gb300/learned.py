@@ -131,22 +131,60 @@ def crop(t, grid, channels, corner, size):
     return v[z:z + size, y:y + size, x:x + size, :].contiguous().view(-1)
 
 
+class _ErrorFields:
+    """Seeded random start errors generated on the GPU for one context (the
+    field-layout activity mask and sample coordinates are kept on the
+    device): white noise, or a sum of smooth random Fourier modes per
+    unknown field; zero on inactive unknowns."""
+
+    def __init__(self, ctx, wl):
+        act = ctx.export(3).to(torch.bool)
+        self.act = act
+        pts = []
+        for kind in _KINDS[wl.dim]:
+            P = workloads.sample_points(kind, wl.n, wl.h, wl.origin)
+            pts.append(torch.stack([torch.from_numpy(np.ascontiguousarray(a).ravel()) for a in P]).cuda())
+        self.pts = pts
+        self.ctx = ctx
+        self.dim = wl.dim
+
+    def white(self, seed):
+        g = torch.Generator(device="cuda").manual_seed(int(seed))
+        e = torch.randn(self.act.numel(), generator=g, device="cuda", dtype=torch.float64) * self.act
+        return self.ctx.fields_to_slots(e)
+
+    def smooth(self, seed, modes=6):
+        rng = np.random.default_rng(seed)
+        parts = []
+        for P in self.pts:
+            f = torch.zeros(P.shape[1], dtype=torch.float64, device="cuda")
+            for _ in range(modes):
+                k = rng.integers(1, 6, self.dim)
+                ph = rng.uniform(0, 2 * np.pi)
+                arg = sum(2 * np.pi * float(k[d]) * P[d] for d in range(self.dim)) + ph
+                f += float(rng.normal()) * torch.sin(arg)
+            parts.append(f)
+        return self.ctx.fields_to_slots(torch.cat(parts) * self.act)
+
+
 def make_cropped_pairs(ctx, wl, n_pairs, seed0, size, cg_iters=(0, 4, 16, 64, 256)):
     """The pairs of make_pairs (pair q: white-noise or smooth start as q is
-    even or odd, cg_iters[q % len] Jacobi-PCG iterations), each cut to a
-    seeded random window of the given size (corner on a multiple of 4, so
-    the network's pooling grid is the one it has on the whole grid); only
-    the windows are kept."""
+    even or odd, cg_iters[q % len] Jacobi-PCG iterations; the start errors
+    drawn on the GPU), each cut to a seeded random window of the given size
+    (corner on a multiple of 4, so the network's pooling grid is the one it
+    has on the whole grid); only the windows are kept.  A window whose
+    target is zero (no active unknown in it) is redrawn, up to 64 times."""
     D, H, W, cin, cout = stokes.learned_grid(ctx)
     rng = np.random.default_rng(seed0)
     lim = [(d - size) // 4 for d in (D, H, W)]
+    ef = _ErrorFields(ctx, wl)
     out = []
     b = ctx.new_vector()
     x = ctx.new_vector()
     r = ctx.new_vector()
     z32 = ctx.new_vector(torch.float32)
     for q in range(n_pairs):
-        e0 = white_error(ctx, seed0 + q) if q % 2 == 0 else smooth_error(ctx, wl, seed0 + q)
+        e0 = ef.white(seed0 + q) if q % 2 == 0 else ef.smooth(seed0 + q)
         k = cg_iters[q % len(cg_iters)]
         e = e0
         if k > 0:
@@ -158,8 +196,12 @@ def make_cropped_pairs(ctx, wl, n_pairs, seed0, size, cg_iters=(0, 4, 16, 64, 25
         feats, rms = stokes.learned_features(ctx, r)
         ctx.apply_preconditioner(0, r.float(), z32)
         targ = stokes.learned_targets(ctx, e - z32.double(), rms)
-        corner = tuple(4 * int(rng.integers(0, m + 1)) if m > 0 else 0 for m in lim)
-        out.append((crop(feats, (D, H, W), cin, corner, size), crop(targ, (D, H, W), cout, corner, size)))
+        for _ in range(64):
+            corner = tuple(4 * int(rng.integers(0, m + 1)) if m > 0 else 0 for m in lim)
+            yc = crop(targ, (D, H, W), cout, corner, size)
+            if float(torch.linalg.norm(yc)) > 0:
+                break
+        out.append((crop(feats, (D, H, W), cin, corner, size), yc))
         del feats, targ
     return out
 
@@ -192,34 +234,41 @@ def init_network(net, seed=0):
     net.set_params(p)
 
 
-def config5(n_train=128, instances=40, pairs_per_instance=50, crop_size=64, epochs=30, batch=4, lr=2e-3,
-            eval_sizes=(128, 128, 256), eval_seed0=9000, train_seed0=5000, max_iter=400000, log=None):
+def config5(n_train=128, instances=20, pairs_per_instance=100, crop_size=64, epochs=30, batch=4, lr=2e-3,
+            eval_sizes=(128, 128, 256), eval_seed0=9000, train_seed0=5000, caps=None, floor=0.01, log=None):
     """The learned preconditioner at scale: solver-generated pairs from 3D
     Gaussian-bump instances (seeds train_seed0..), cut to crop_size^3
     windows, train the BF16 U-Net on the tensor cores, then solve held-out
     instances (seeds eval_seed0.., sizes eval_sizes) with the learned
     flexible CG, the same mixed-precision CG with Jacobi alone, and plain
-    FP64 Jacobi-PCG.  Returns a dict of timings, losses and per-instance
-    comparisons."""
+    FP64 Jacobi-PCG, each capped at caps[size] iterations (these systems are
+    stiff: plain FP64 Jacobi-PCG needs 2.6e5 iterations at 64^3).  ``floor``
+    is the face-mass floor of stokes_set_min_face_liquid for every instance
+    (0: the paper's system).  Returns timings, losses and per-instance
+    comparisons (status, iterations, device ms, final true residual)."""
     from . import workloads as W
     say = log or (lambda *a: None)
+    caps = caps or {128: 100000, 256: 60000}
     t0 = time.perf_counter()
     data = []
-    cin = cout = None
+    net = None
+    # the network grid of an n^3 instance is (n + 1) rounded up to a multiple of 4
+    eval_grids = [(s + 4) // 4 * 4 for s in eval_sizes]
+    max_vox = max([batch * crop_size ** 3, ((n_train + 4) // 4 * 4) ** 3] + [g ** 3 for g in eval_grids])
     for i in range(instances):
         wl = W.bumps_3d(n_train, seed=train_seed0 + i)
-        ctx, dev = stokes.context_for(wl)
-        D, H, Wd, cin, cout = stokes.learned_grid(ctx)
+        ctx, dev = stokes.context_for(wl, min_face_liquid=floor)
+        if net is None:
+            D, H, Wd, cin, cout = stokes.learned_grid(ctx)
+            net = stokes.Net(3, cin, cout, max_vox)
+            init_network(net, seed=3)
+        stokes.attach_network(ctx, net)           # the features are formed on the network's grid
         data += make_cropped_pairs(ctx, wl, pairs_per_instance, seed0=100000 * (i + 1), size=crop_size)
         ctx.close()
         del dev
         torch.cuda.empty_cache()
     t_data = time.perf_counter() - t0
     say(f"pairs: {len(data)} in {t_data:.1f} s")
-    eval_grids = [(s + 4) // 4 * 4 for s in eval_sizes]
-    max_vox = max([batch * crop_size ** 3] + [g ** 3 for g in eval_grids])
-    net = stokes.Net(3, cin, cout, max_vox)
-    init_network(net, seed=3)
     t0 = time.perf_counter()
     losses = train(net, data, (crop_size,) * 3, epochs=epochs, batch=batch, lr=lr, log=say)
     torch.cuda.synchronize()
@@ -229,12 +278,14 @@ def config5(n_train=128, instances=40, pairs_per_instance=50, crop_size=64, epoc
     rows = []
     for k, size in enumerate(eval_sizes):
         wl = W.bumps_3d(size, seed=eval_seed0 + k)
-        ctx, dev = stokes.context_for(wl)
-        row = dict(n=size, seed=eval_seed0 + k, **compare_solvers(ctx, dev, net, max_iter=max_iter))
+        ctx, dev = stokes.context_for(wl, min_face_liquid=floor)
+        row = dict(n=size, seed=eval_seed0 + k, cap=caps.get(size, 30000),
+                   **compare_solvers(ctx, dev, net, max_iter=caps.get(size, 30000)))
         say(f"eval {size}^3: {row}")
         rows.append(row)
         ctx.close()
         del dev
         torch.cuda.empty_cache()
     return dict(pairs=instances * pairs_per_instance, crop=crop_size, instances=instances, n_train=n_train,
-                params=int(net.n), epochs=epochs, train_loss=losses, s_pairs=t_data, s_train=t_train, eval=rows)
+                params=int(net.n), epochs=epochs, floor=floor, train_loss=losses, s_pairs=t_data, s_train=t_train,
+                eval=rows)
