@@ -30,7 +30,7 @@ template <class T, class C> __device__ __forceinline__ T ld(const C* p, int64_t 
 template <> __device__ __forceinline__ double ld<double, double>(const double* p, int64_t o) { return __ldg(p + o); }
 template <> __device__ __forceinline__ float ld<float, float>(const float* p, int64_t o) { return __ldg(p + o); }
 template <> __device__ __forceinline__ float ld<float, __nv_bfloat16>(const __nv_bfloat16* p, int64_t o) {
-    return __bfloat162float(p[o]);
+    return __bfloat162float(__ldg(p + o));      // read-only path, as for the FP32 and FP64 coefficients
 }
 
 template <class T, int MODE>

@@ -217,14 +217,16 @@ __global__ void __launch_bounds__(256) k_sw_init(Layout L, const int* __restrict
     }
 }
 
-// (at most 48 registers: five CTAs share an SM, each taking two tiles per
-// round, so up to 1,520 active tiles are one wave; the dots are float-float,
-// not FP64, whose arithmetic is slow on this part)
-template <int INIT>
-__global__ void __launch_bounds__(256, 5) k_sw_finish(Layout L, const int* __restrict__ tiles, DevArrays D,
+// (five CTAs share an SM, each taking two tiles per round, so up to 1,520
+// active tiles are one wave; the dots are float-float, not FP64, whose
+// arithmetic is slow on this part).  UPD: the CG step's x += alpha p,
+// r -= alpha q is done here for every slot of the tile (the local solves
+// read r - alpha q), so no separate update kernel runs.
+template <int INIT, int UPD = 0>
+__global__ void __launch_bounds__(256, UPD ? 3 : 5) k_sw_finish(Layout L, const int* __restrict__ tiles, DevArrays D,
                                                    SchwarzPlan P, CgWork<float> w, CgScalars* sc, double* partial,
                                                    unsigned* counter, int ntiles, cudaGraphConditionalHandle h,
-                                                   int use_cond) {
+                                                   int use_cond, const float* __restrict__ pdir = nullptr) {
     if (!INIT && sc->done) {
         if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
         return;
@@ -236,16 +238,20 @@ __global__ void __launch_bounds__(256, 5) k_sw_finish(Layout L, const int* __res
     for (int k = blockIdx.x; k < ntiles; k += 2 * gridDim.x) {
         const int k2 = k + gridDim.x;
         SwGather g0, g1;
+        SwUpdate u0, u1;
         const int t0 = tiles[k];
         sw_gather_load(L, D, P, w.r, (t0 % L.ntx) * TX + (threadIdx.x & 31), (t0 / L.ntx) * TY2 + (threadIdx.x >> 5),
                        g0);
+        if (UPD) sw_update_load(L, w, pdir, g0.o, u0);
         if (k2 < ntiles) {
             const int t1 = tiles[k2];
             sw_gather_load(L, D, P, w.r, (t1 % L.ntx) * TX + (threadIdx.x & 31),
                            (t1 / L.ntx) * TY2 + (threadIdx.x >> 5), g1);
+            if (UPD) sw_update_load(L, w, pdir, g1.o, u1);
         }
-        sw_gather_finish(L, g0, w.z, rz, rr);
-        if (k2 < ntiles) sw_gather_finish(L, g1, w.z, rz, rr);
+        const float alpha = UPD ? (float)sc->alpha : 0.f;
+        sw_gather_finish(L, g0, w.z, rz, rr, UPD ? &u0 : nullptr, alpha, w.r, w.x);
+        if (k2 < ntiles) sw_gather_finish(L, g1, w.z, rz, rr, UPD ? &u1 : nullptr, alpha, w.r, w.x);
     }
     block_partial2(rz.warp(), rr.warp(), partial, counter, gridDim.x, [&](double trz, double trr) {
         if (INIT) {
@@ -362,10 +368,11 @@ static void schwarz_body(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, i
     a.counter = c->counter;
     a.sc = c->sc;
     launch_apply_mode<float, float>(L, c->tiles, nb, c->coef<float>(), w.z, w.q, MODE_CG, a, s);
-    k_cg_xr<<<persist_grid((const void*)k_cg_xr, nb), 256, 0, s>>>(L, c->tiles, nb, c->nf, w, w.p[parity ^ 1], c->sc);
-    launch_schwarz_gemv(L, *c->sw, w.r, c->sc, s);
-    k_sw_finish<0><<<persist_grid((const void*)k_sw_finish<0>, (nb + 1) / 2), 256, 0, s>>>(L, c->tiles, c->A, *c->sw, w, c->sc,
-                                                                               c->partial, c->counter, nb, h, use_cond);
+    // the step's x += alpha p, r -= alpha q: the local solves read r - alpha q
+    // and the gather writes both for every slot
+    launch_schwarz_gemv(L, *c->sw, w.r, c->sc, s, w.q);
+    k_sw_finish<0, 1><<<persist_grid((const void*)k_sw_finish<0, 1>, (nb + 1) / 2), 256, 0, s>>>(
+        L, c->tiles, c->A, *c->sw, w, c->sc, c->partial, c->counter, nb, h, use_cond, w.p[parity ^ 1]);
 }
 
 static void schwarz_start(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
@@ -881,6 +888,21 @@ static cudaError_t bench_impl(Ctx* c, CgWork<T>& w, const T* minv, const Coef<C>
     k_cg_init<T><<<nb, 256, 0, s>>>(L, c->tiles, c->nf, c->b64, minv, w, c->sc, c->partial, c->counter, nb, h0, 0);
     std::vector<cudaEvent_t> ev(2 * launches + 1);
     for (auto& x : ev) cudaEventCreate(&x);
+    // two untimed iterations first: the first launch of a kernel in a process
+    // can wait on the host (module loading), which the events would count
+    for (int k = -2; k < 0; ++k) {
+        ApplyArgs a{};
+        a.pold = w.p[k & 1];
+        a.pnew = w.p[(k & 1) ^ 1];
+        a.partial = c->partial;
+        a.counter = c->counter;
+        a.sc = c->sc;
+        launch_apply_mode<T, C>(L, c->tiles, nb, cf, w.z, w.q, MODE_CG, a, s);
+        k_cg_update<T><<<persist_grid((const void*)k_cg_update<T>, nb), 256, 0, s>>>(L, c->tiles, c->nf, minv, w,
+                                                                                   w.p[(k & 1) ^ 1], c->sc, c->partial,
+                                                                                   c->counter, nb, h0, 0);
+    }
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     cudaEventRecord(ev[0], s);
     for (int k = 0; k < launches; ++k) {
         ApplyArgs a{};
@@ -929,8 +951,8 @@ cudaError_t bench_schwarz_kernels(Ctx* c, int launches, double* ms_local, double
         return e;
     double by = 0.0;
     for (int q = 0; q < P.np; ++q)
-        by += (double)sw_patch_bytes(nloc[q]) + PMAX * (sizeof(float) + sizeof(float) + sizeof(short)) +
-              2 * PR * PR * sizeof(float) + 2 * sizeof(int);
+        by += (double)sw_patch_bytes(nloc[q]) + PMAX * (sizeof(float) + sizeof(float) + sizeof(float) + sizeof(short)) +
+              2 * PR * PR * sizeof(float) + 2 * sizeof(int);   // factor; r, q, scaling, map; results; corner, count
     *bytes_local = by;
     if ((e = push_inner_params(c, 1.0, 0.0, 1 << 30)) != cudaSuccess) return e;
     CgWork<float>& w = c->w32;
@@ -941,12 +963,21 @@ cudaError_t bench_schwarz_kernels(Ctx* c, int launches, double* ms_local, double
                                                                                c->partial, c->counter, nb, 0, 0);
     std::vector<cudaEvent_t> ev(2 * launches + 1);
     for (auto& x : ev) cudaEventCreate(&x);
+    // two untimed iterations first: the first launch of a kernel in a process
+    // can wait on the host (module loading), which the events would count
+    // the kernels as the CG loop runs them (alpha = 0 here: r and x keep their values)
+    for (int k = 0; k < 2; ++k) {
+        launch_schwarz_gemv(L, P, w.r, c->sc, s, w.q);
+        k_sw_finish<0, 1><<<persist_grid((const void*)k_sw_finish<0, 1>, (nb + 1) / 2), 256, 0, s>>>(
+            L, c->tiles, c->A, P, w, c->sc, c->partial, c->counter, nb, 0, 0, w.p[0]);
+    }
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     cudaEventRecord(ev[0], s);
     for (int k = 0; k < launches; ++k) {
-        launch_schwarz_gemv(L, P, w.r, c->sc, s);
+        launch_schwarz_gemv(L, P, w.r, c->sc, s, w.q);
         cudaEventRecord(ev[2 * k + 1], s);
-        k_sw_finish<0><<<persist_grid((const void*)k_sw_finish<0>, (nb + 1) / 2), 256, 0, s>>>(L, c->tiles, c->A, P, w, c->sc,
-                                                                                   c->partial, c->counter, nb, 0, 0);
+        k_sw_finish<0, 1><<<persist_grid((const void*)k_sw_finish<0, 1>, (nb + 1) / 2), 256, 0, s>>>(
+            L, c->tiles, c->A, P, w, c->sc, c->partial, c->counter, nb, 0, 0, w.p[0]);
         cudaEventRecord(ev[2 * k + 2], s);
     }
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;

@@ -292,8 +292,10 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
 // that never completes (bounded wait) marks the solve STOKES_ERR_TIMEOUT and
 // ends it.  With the test hook (sc->wait_test) no copy is issued, so the
 // wait runs out after SW_TEST_POLLS polls and nothing is left in flight.
+// Given q, the residual read is r - alpha q (alpha of this CG step): the
+// step's update of r is written later by the gather, for every slot once.
 __global__ void __launch_bounds__(128, 15) k_schwarz_gemv(Layout L, SchwarzPlan P, const float* __restrict__ r,
-                                                      CgScalars* sc) {
+                                                      const float* __restrict__ q, CgScalars* sc) {
     extern __shared__ __align__(128) uint8_t Fs[];             // SW_FAC_BYTES
     __shared__ __align__(16) float s[PMAX8];
     __shared__ float y[PMAX];
@@ -306,6 +308,7 @@ __global__ void __launch_bounds__(128, 15) k_schwarz_gemv(Layout L, SchwarzPlan 
     const uint32_t b_addr = smem_u32(&bar);
     const int n = P.nloc[p];
     const bool stall = sc->wait_test != 0;
+    const float alpha = q ? (float)sc->alpha : 0.f;
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_addr), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -329,12 +332,13 @@ __global__ void __launch_bounds__(128, 15) k_schwarz_gemv(Layout L, SchwarzPlan 
         kk = map[e];
         sa = scl[e];
         if (e >= PR * PR) {
-            const float rv = r[L.stride + o];
+            const float rv = q ? r[L.stride + o] - alpha * q[L.stride + o] : r[L.stride + o];
             if (kk >= 0) s[kk] = rv * sa;
         } else {
             kp = map[2 * PR * PR + e];
             sb = scl[2 * PR * PR + e];
-            const float rt = r[o], rp = r[2 * L.stride + o];
+            const float rt = q ? r[o] - alpha * q[o] : r[o];
+            const float rp = q ? r[2 * L.stride + o] - alpha * q[2 * L.stride + o] : r[2 * L.stride + o];
             // the scaling belongs to the rotated unknowns: rotate, then scale
             if (kk >= 0 && kp >= 0) {
                 s[kk] = (rt + rp) * H * sa;
@@ -381,8 +385,8 @@ __global__ void __launch_bounds__(128, 15) k_schwarz_gemv(Layout L, SchwarzPlan 
 constexpr int SW_GEMV_SMEM = SW_FAC_BYTES;
 
 static inline void launch_schwarz_gemv(const Layout& L, const SchwarzPlan& P, const float* r, CgScalars* sc,
-                                       cudaStream_t s) {
-    if (P.np) k_schwarz_gemv<<<P.np, 128, SW_GEMV_SMEM, s>>>(L, P, r, sc);
+                                       cudaStream_t s, const float* q = nullptr) {
+    if (P.np) k_schwarz_gemv<<<P.np, 128, SW_GEMV_SMEM, s>>>(L, P, r, q, sc);
 }
 
 // z at one slot (c, rr) from the patches' local results, in two parts so
@@ -396,6 +400,22 @@ struct SwGather {
     bool act[3], use[4], real;
     int64_t o;
 };
+// The CG update fused into the gather (x += alpha p, r -= alpha q for the
+// slot itself): the slot's q, x and p.
+struct SwUpdate {
+    float qv[3], xv[3], pv[3];
+};
+
+__device__ __forceinline__ void sw_update_load(const Layout& L, const CgWork<float>& w, const float* __restrict__ p,
+                                               int64_t o, SwUpdate& u) {
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        const int64_t of = (int64_t)f * L.stride + o;
+        u.qv[f] = __ldg(w.q + of);
+        u.xv[f] = w.x[of];
+        u.pv[f] = __ldg(p + of);
+    }
+}
 
 __device__ __forceinline__ void sw_gather_load(const Layout& L, const DevArrays& D, const SchwarzPlan& P,
                                                const float* __restrict__ r, int c, int rr, SwGather& g) {
@@ -429,10 +449,20 @@ __device__ __forceinline__ void sw_gather_load(const Layout& L, const DevArrays&
     }
 }
 
-__device__ __forceinline__ void sw_gather_finish(const Layout& L, const SwGather& g, float* __restrict__ z,
-                                                 AccT<float>& rz, AccT<float>& r2) {
+// With an update u (and alpha): r -= alpha q and x += alpha p are written
+// first, and z, r.z, r.r use the new r.
+__device__ __forceinline__ void sw_gather_finish(const Layout& L, SwGather& g, float* __restrict__ z,
+                                                 AccT<float>& rz, AccT<float>& r2, const SwUpdate* u = nullptr,
+                                                 float alpha = 0.f, float* __restrict__ r = nullptr,
+                                                 float* __restrict__ x = nullptr) {
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
+        if (u) {
+            const int64_t of = (int64_t)f * L.stride + g.o;
+            g.rv[f] = g.rv[f] - alpha * u->qv[f];
+            r[of] = g.rv[f];
+            x[of] = u->xv[f] + alpha * u->pv[f];
+        }
         float s = 0.f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) s += g.use[q] ? g.v[f][q] : 0.f;
@@ -440,34 +470,6 @@ __device__ __forceinline__ void sw_gather_finish(const Layout& L, const SwGather
         z[(int64_t)f * L.stride + g.o] = zv;
         rz.add(g.rv[f], zv);          // float-float: FP64 arithmetic is slow on this part
         r2.add(g.rv[f], g.rv[f]);
-    }
-}
-
-// x += alpha p, r -= alpha q (FP32), no preconditioning; persistent over the
-// tile list
-__global__ void __launch_bounds__(256) k_cg_xr(Layout L, const int* __restrict__ tiles, int ntiles, int nf,
-                                               CgWork<float> w, const float* __restrict__ p, const CgScalars* sc) {
-    if (sc->done) return;
-    const float alpha = (float)sc->alpha;
-    float* __restrict__ X = w.x;
-    float* __restrict__ R = w.r;
-    const float* __restrict__ Q = w.q;
-    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
-        const int tile = tiles[k];
-        const int c0 = (tile % L.ntx) * TX, r0 = (tile / L.ntx) * TY2;
-        const int64_t o = L.off(c0 + (threadIdx.x & 31), r0 + (threadIdx.x >> 5), 0);
-        float pv[3], xv[3], rv[3], qv[3];
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            const int64_t of = (int64_t)f * L.stride + o;
-            pv[f] = __ldg(p + of); xv[f] = X[of]; rv[f] = R[of]; qv[f] = __ldg(Q + of);
-        }
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            const int64_t of = (int64_t)f * L.stride + o;
-            X[of] = xv[f] + alpha * pv[f];
-            R[of] = rv[f] - alpha * qv[f];
-        }
     }
 }
 
