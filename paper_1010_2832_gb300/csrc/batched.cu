@@ -263,8 +263,7 @@ __global__ void __launch_bounds__(256) k_batched(const BInst* __restrict__ inst,
     Smem2<double, TY>& sm = *reinterpret_cast<Smem2<double, TY>*>(smraw);
     uint8_t* Fs = reinterpret_cast<uint8_t*>(smraw);
     __shared__ __align__(16) float ls[SW ? PMAX8 : 4];
-    __shared__ float ly[SW ? PMAX : 4];
-    __shared__ __align__(16) __half lhb[SW ? 2 * 16 * 7 : 8];
+    __shared__ __align__(16) __half lhb[SW ? SW_HB_HALVES : 8];
     __shared__ __align__(8) unsigned long long lbar;
     __shared__ int lok;
     uint32_t uses = 0;
@@ -338,7 +337,7 @@ __global__ void __launch_bounds__(256) k_batched(const BInst* __restrict__ inst,
                 volatile BState* vs = st + i;
                 if (vs->done) continue;
                 const double alpha = vs->mode == 0 ? vs->alpha : 0.0;
-                batched_local_solve(inst[i], pl_patch[k], alpha, Fs, ls, ly, lhb, &lbar, uses, lok, g);
+                batched_local_solve(inst[i], pl_patch[k], alpha, Fs, ls, ls, lhb, &lbar, uses, lok, g);
             }
             if (!grid_sync(g, nb)) return;
         }

@@ -297,25 +297,27 @@ __global__ void __launch_bounds__(256) k_schwarz_setup(Layout L, DevArrays D, co
 __global__ void __launch_bounds__(128, 15) k_schwarz_gemv(Layout L, SchwarzPlan P, const float* __restrict__ r,
                                                       const float* __restrict__ q, CgScalars* sc) {
     extern __shared__ __align__(128) uint8_t Fs[];             // SW_FAC_BYTES
-    __shared__ __align__(16) float s[PMAX8];
-    __shared__ float y[PMAX];
-    __shared__ __align__(16) __half hb[2 * 16 * 7];
+    __shared__ __align__(16) float s[PMAX8];            // r_p, then (as y) X~ r_p, then z_p
+    __shared__ __align__(16) __half hb[SW_HB_HALVES];
     __shared__ __align__(8) unsigned long long bar;
     __shared__ int ok_s;
-    if (sc->done) return;
     const int t = threadIdx.x;
     const int p = blockIdx.x;
     const uint32_t b_addr = smem_u32(&bar);
-    const int n = P.nloc[p];
+    // the patch's size and corner and the solve's scalars are loaded together
+    // (one memory round trip before the copy starts)
+    const int n = P.nloc[p], cw = P.corner[p];
+    const int done = sc->done;
     const bool stall = sc->wait_test != 0;
     const float alpha = q ? (float)sc->alpha : 0.f;
+    if (done) return;
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b_addr), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         if (!stall) sw_issue(b_addr, Fs, P.fac + (int64_t)p * SW_FAC_BYTES, sw_patch_bytes(n), P.evict_first != 0);
     }
     constexpr float H = 0.70710678118654752f;
-    const int I = P.corner[p] & 0xffff, J = P.corner[p] >> 16;
+    const int I = cw & 0xffff, J = cw >> 16;
     const int a0 = PB * I - 1, b0 = PB * J - 1;
     const short* map = P.lmap + (int64_t)p * PMAX;
     const float* scl = P.scale + (int64_t)p * PMAX;
@@ -362,7 +364,7 @@ __global__ void __launch_bounds__(128, 15) k_schwarz_gemv(Layout L, SchwarzPlan 
         }
         return;
     }
-    sw_factor_products(Fs, n, s, y, hb);
+    sw_factor_products(Fs, n, s, s, hb);
     // scale, rotate back and store by position
     float* out = P.ybuf + (int64_t)(J * P.npx + I) * PMAX;
     if (t < 2 * PR * PR) {

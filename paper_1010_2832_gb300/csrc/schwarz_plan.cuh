@@ -158,17 +158,6 @@ __device__ __forceinline__ void sw_hl_scale(float m, float& sc, float& inv) {
     inv = __int_as_float((127 - k) << 23);
 }
 
-// Largest |v[k]| over k < n, reduced by every warp on its own.
-__device__ __forceinline__ float sw_warp_absmax(const float* v, int n, int lane) {
-    unsigned m = 0u;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int k = lane + 32 * q;
-        if (k < n) m = max(m, __float_as_uint(fabsf(v[k])));
-    }
-    return __uint_as_float(__reduce_max_sync(0xffffffffu, m));
-}
-
 // Split of the vector v (n entries, scaled by sc) into FP16 hi + lo parts,
 // one entry per thread (threads 0..111), into hb[0][.] and hb[1][.]; entries
 // from n to 111 are zero.
@@ -182,130 +171,174 @@ __device__ __forceinline__ void sw_split(const float* v, int n, float sc, __half
     }
 }
 
-// B fragment of k-tile kt from the split vector: lane (g, t) = (lane / 4,
-// lane % 4) holds B[2t, 2t+1][g] and B[2t+8, 2t+9][g]; column 0 is the hi
-// part, column 1 the lo part, columns 2..7 zero.
-__device__ __forceinline__ void sw_b_frag(const __half* hb, int kt, int lane, uint32_t& b0, uint32_t& b1) {
-    const int g = lane >> 2, t = lane & 3;
-    if (g < 2) {
-        const uint32_t* p = reinterpret_cast<const uint32_t*>(hb + 16 * 7 * g + 16 * kt + 2 * t);
-        b0 = p[0];
-        b1 = p[4];
-    } else {
-        b0 = b1 = 0u;
+// Shared scratch of sw_factor_products, in halves: the split vector (hi,
+// lo), the row table (one 32-bit word per stored row) and the four warps'
+// largest magnitudes (one word each).
+constexpr int SW_HB_HALVES = 2 * 16 * 7 + 2 * 16 * 7 + 2 * 4;
+
+// Largest |v[k]| over k < n (up to 128 entries), every thread of warps 0..3
+// taking one entry: a warp reduction, the four warps' results through wm,
+// one barrier (every thread of the CTA must call it).
+__device__ __forceinline__ float sw_cta_absmax(const float* v, int n, unsigned* wm) {
+    const int t = threadIdx.x, warp = t >> 5;
+    if (warp < 4) {
+        const unsigned m = __reduce_max_sync(0xffffffffu, t < n ? __float_as_uint(fabsf(v[t])) : 0u);
+        if ((t & 31) == 0) wm[warp] = m;
+    }
+    __syncthreads();
+    const uint4 a = *reinterpret_cast<const uint4*>(wm);
+    return __uint_as_float(max(max(a.x, a.y), max(a.z, a.w)));
+}
+
+// y = X~ s for the row tiles MA and MB (MB < MA; MB < 0: none) of one warp:
+// row tile m costs m + 1 tile products (k-tiles 0..m), the two chains
+// interleaved.  hbw: the split vector as words (lane's B fragment of k-tile
+// kt at hbw[lb + 8 kt] and hbw[lb + 8 kt + 4]); rowtab: the row table.
+template <int MA, int MB>
+__device__ __forceinline__ void sw_rows(uint32_t X, int ntile, int lane, const uint32_t* hbw, int lb,
+                                        const uint32_t* rowtab, float (&dA)[4], float (&dB)[4]) {
+    const int li = lane >> 3, lj = lane & 7;      // ldmatrix: matrix li, its row lj
+    const bool onA = MA < ntile, onB = MB >= 0 && MB < ntile;
+    const uint32_t eA = rowtab[16 * MA + (li & 1) * 8 + lj], sA = eA >> 16;
+    const uint32_t aA = X + (eA & 0xffffu) + (uint32_t)(li >> 1) * (sA >> 1);
+    uint32_t aB = 0, sB = 0;
+    if (MB >= 0) {
+        const uint32_t eB = rowtab[16 * (MB < 0 ? 0 : MB) + (li & 1) * 8 + lj];
+        sB = eB >> 16;
+        aB = X + (eB & 0xffffu) + (uint32_t)(li >> 1) * (sB >> 1);
+    }
+#pragma unroll
+    for (int kt = 0; kt <= MA; ++kt) {
+        if (kt >= ntile) break;                          // no chain reaches this k-tile
+        const uint32_t b0 = hbw[lb + 8 * kt], b1 = hbw[lb + 8 * kt + 4];
+        uint32_t a[4];
+        if (onA) {
+            ldsm_x4(a, aA + sA * kt);
+            if (kt == MA) a[2] = 0u;                     // upper 8 x 8 block of the diagonal tile
+            mma_f16_16816(dA, a, b0, b1);
+        }
+        if (kt <= MB && onB) {
+            ldsm_x4(a, aB + sB * kt);
+            if (kt == MB) a[2] = 0u;
+            mma_f16_16816(dB, a, b0, b1);
+        }
+    }
+}
+
+// z = X~^T v for the column tiles CA and CB (CA < CB; CB > 6: none) of one
+// warp: column tile c costs 7 - c tile products (row tiles c..6, the
+// transposed tiles by ldmatrix.trans), the two chains interleaved.
+template <int CA, int CB>
+__device__ __forceinline__ void sw_cols(uint32_t X, int ntile, int lane, const uint32_t* hbw, int lb,
+                                        const uint32_t* rowtab, float (&dA)[4], float (&dB)[4]) {
+    const int li = lane >> 3, lj = lane & 7;
+#pragma unroll
+    for (int rt = CA; rt < 7; ++rt) {
+        if (rt >= ntile) break;
+        const uint32_t e = rowtab[16 * rt + (li >> 1) * 8 + lj], st = e >> 16;
+        const uint32_t addr = X + (e & 0xffffu) + (uint32_t)(li & 1) * (st >> 1);
+        const uint32_t b0 = hbw[lb + 8 * rt], b1 = hbw[lb + 8 * rt + 4];
+        uint32_t a[4];
+        ldsm_x4_trans(a, addr + st * CA);
+        if (rt == CA) a[1] = 0u;                         // upper 8 x 8 block of the diagonal tile
+        mma_f16_16816(dA, a, b0, b1);
+        if (CB <= 6 && rt >= CB) {
+            ldsm_x4_trans(a, addr + st * (CB <= 6 ? CB : 0));
+            if (rt == CB) a[1] = 0u;
+            mma_f16_16816(dB, a, b0, b1);
+        }
     }
 }
 
 // s <- X~^T diag(rho^2) X~ s for the stored factor F of an n-unknown patch in
 // shared memory, by warps 0-3 of the CTA (every thread of the CTA must call
-// it).  X~ is cut into 16 x 16 tiles (rows and columns up to 112); tiles
-// wholly above the diagonal are skipped and the upper 8 x 8 block of each
-// diagonal tile (not stored: rows of the first half hold 8 columns fewer) is
-// zeroed in the fragment.  y = X~ s: output tile m costs m + 1 tile
-// products, so warps 0..3 take tiles {6}, {5, 0}, {4, 1}, {3, 2} (7 each,
-// the two chains of a warp interleaved); z = X~^T (rho^2 y): output tile c
-// costs 7 - c, so {0}, {1, 6}, {2, 5}, {3, 4}.  Tile addresses of rows at
-// or past n point at row 0 (finite data): their outputs are dropped (first
-// product) or meet zero vector entries (second product).  Each vector is
-// split into FP16 hi + lo once, one entry per thread, into hb (2 x 112
-// halves of shared memory).  s holds PMAX8 floats (entries from n on are
-// not read); y holds PMAX floats of scratch.  Ends after a barrier with z in
-// s[0, n).
+// it, with at least 112 threads).  X~ is cut into 16 x 16 tiles (rows and
+// columns up to 112); tiles wholly above the diagonal are skipped and the
+// upper 8 x 8 block of each diagonal tile (not stored: rows of the first
+// half hold 8 columns fewer) is zeroed in the fragment.  y = X~ s: output
+// tile m costs m + 1 tile products, so warps 0..3 take tiles {6}, {5, 0},
+// {4, 1}, {3, 2} (7 each, the two chains of a warp interleaved); z = X~^T
+// (rho^2 y): output tile c costs 7 - c, so {0}, {1, 6}, {2, 5}, {3, 4}.
+// Each warp runs its own tile lists unrolled at compile time (one code path
+// per warp) and takes its tile addresses from a row table built once per
+// patch (byte offset of the row's first column block and the step to the
+// next 16 columns; rows at or past n point at row 0, whose data is finite:
+// their outputs are dropped in the first product and meet zero vector
+// entries in the second), so a tile costs its ldmatrix, its mma and one
+// address add.  Each vector is split into FP16 hi + lo once, one entry per
+// thread.  hb: SW_HB_HALVES halves of shared memory (16-byte aligned); s
+// holds PMAX8 floats (entries from n on are not read); y holds PMAX8 floats
+// of scratch and may be s itself (s is not read once split).  Ends after a
+// barrier with z in s[0, n) (entries from n to the last tile's end hold
+// finite values that callers do not read).
 __device__ __forceinline__ void sw_factor_products(const uint8_t* F, int n, float* s, float* y, __half* hb) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const float* rs = reinterpret_cast<const float*>(F);
     const uint32_t X = smem_u32(F + SW_RS_BYTES);
-    const int g = lane >> 2, t = lane & 3;
-    const int li = lane >> 3, lj = lane & 7;      // ldmatrix: matrix li, its row lj
+    uint32_t* rowtab = reinterpret_cast<uint32_t*>(hb + 2 * 16 * 7);
+    unsigned* wm = reinterpret_cast<unsigned*>(hb + 4 * 16 * 7);
+    const uint32_t* hbw = reinterpret_cast<const uint32_t*>(hb);
+    const int g = lane >> 2, tq = lane & 3;
+    // word of the lane's B fragment: columns 0 (hi) and 1 (lo) are the split
+    // vector; columns 2..7 repeat them, and their outputs are not read
+    const int lb = 56 * (g & 1) + tq;
     const int ntile = (n + 15) >> 4;
-    float sc = 1.f, inv = 1.f;
-    if (warp < 4) sw_hl_scale(sw_warp_absmax(s, n, lane), sc, inv);
+    if (t < 16 * 7) {
+        const int row = t < n ? t : 0;
+        const uint32_t R = (uint32_t)row >> 3, w = (uint32_t)min(8, n - 8 * (int)R);
+        rowtab[t] = (2u * (32u * R * (R + 1u) + (uint32_t)(row & 7) * 8u)) | ((32u * w) << 16);
+    }
+    float sc, inv;
+    sw_hl_scale(sw_cta_absmax(s, n, wm), sc, inv);
     sw_split(s, n, sc, hb);
     __syncthreads();
     if (warp < 4) {
-        const int mA = 6 - warp, mB = warp - 1;           // mB < mA; mB = -1 for warp 0
         float dA[4] = {0.f, 0.f, 0.f, 0.f}, dB[4] = {0.f, 0.f, 0.f, 0.f};
-        int rowA = 16 * mA + (li & 1) * 8 + lj, rowB = 16 * max(mB, 0) + (li & 1) * 8 + lj;
-        rowA = rowA < n ? rowA : 0;
-        rowB = rowB < n ? rowB : 0;
-        // column block (li >> 1) of the first k-tile; the next k-tile is two
-        // blocks (16 k halves, k = rows kept in the row's band) further on
-        const uint32_t baseA = X + 2u * (uint32_t)sw_fac_off(rowA, (li >> 1) * 8, n);
-        const uint32_t baseB = X + 2u * (uint32_t)sw_fac_off(rowB, (li >> 1) * 8, n);
-        const uint32_t stepA = 32u * (uint32_t)min(8, n - 8 * (rowA / 8));
-        const uint32_t stepB = 32u * (uint32_t)min(8, n - 8 * (rowB / 8));
-        const bool onA = mA < ntile, onB = mB >= 0 && mB < ntile;
-#pragma unroll
-        for (int kt = 0; kt < 7; ++kt) {
-            if (kt >= ntile) break;
-            uint32_t b0, b1;
-            sw_b_frag(hb, kt, lane, b0, b1);
-            if (onA && kt <= mA) {
-                uint32_t a[4];
-                ldsm_x4(a, baseA + stepA * kt);
-                if (kt == mA) a[2] = 0u;                 // upper 8 x 8 block of the diagonal tile
-                mma_f16_16816(dA, a, b0, b1);
-            }
-            if (onB && kt <= mB) {
-                uint32_t a[4];
-                ldsm_x4(a, baseB + stepB * kt);
-                if (kt == mB) a[2] = 0u;
-                mma_f16_16816(dB, a, b0, b1);
-            }
+        switch (warp) {
+            case 0: sw_rows<6, -1>(X, ntile, lane, hbw, lb, rowtab, dA, dB); break;
+            case 1: sw_rows<5, 0>(X, ntile, lane, hbw, lb, rowtab, dA, dB); break;
+            case 2: sw_rows<4, 1>(X, ntile, lane, hbw, lb, rowtab, dA, dB); break;
+            default: sw_rows<3, 2>(X, ntile, lane, hbw, lb, rowtab, dA, dB); break;
         }
-        if (t == 0) {
-            if (onA) {
+        if (tq == 0) {
+            const int mA = 6 - warp, mB = warp - 1;
+            // rows from n to the tile's end get finite values that are not read
+            if (mA < ntile) {
                 const int r0 = 16 * mA + g, r1 = r0 + 8;
-                if (r0 < n) y[r0] = (dA[0] + dA[1]) * inv * rs[r0];
-                if (r1 < n) y[r1] = (dA[2] + dA[3]) * inv * rs[r1];
+                y[r0] = (dA[0] + dA[1]) * inv * rs[r0];
+                y[r1] = (dA[2] + dA[3]) * inv * rs[r1];
             }
-            if (onB) {
+            if (mB >= 0 && mB < ntile) {
                 const int r0 = 16 * mB + g, r1 = r0 + 8;
-                if (r0 < n) y[r0] = (dB[0] + dB[1]) * inv * rs[r0];
-                if (r1 < n) y[r1] = (dB[2] + dB[3]) * inv * rs[r1];
+                y[r0] = (dB[0] + dB[1]) * inv * rs[r0];
+                y[r1] = (dB[2] + dB[3]) * inv * rs[r1];
             }
         }
     }
     __syncthreads();
-    if (warp < 4) sw_hl_scale(sw_warp_absmax(y, n, lane), sc, inv);
+    sw_hl_scale(sw_cta_absmax(y, n, wm), sc, inv);
     sw_split(y, n, sc, hb);          // hb of the first product is no longer read
     __syncthreads();
     if (warp < 4) {
-        const int cA = warp, cB = 7 - warp;               // cB = 7 (none) for warp 0
         float dA[4] = {0.f, 0.f, 0.f, 0.f}, dB[4] = {0.f, 0.f, 0.f, 0.f};
-        const int cofsA = 16 * cA + (li & 1) * 8, cofsB = 16 * min(cB, 6) + (li & 1) * 8;
-        const bool onA = cA < ntile, onB = cB <= 6 && cB < ntile;
-#pragma unroll
-        for (int rt = 0; rt < 7; ++rt) {
-            if (rt >= ntile) break;
-            uint32_t b0, b1;
-            sw_b_frag(hb, rt, lane, b0, b1);
-            int row = 16 * rt + (li >> 1) * 8 + lj;
-            row = row < n ? row : 0;
-            if (onA && rt >= cA) {
-                uint32_t a[4];
-                ldsm_x4_trans(a, X + 2u * (uint32_t)sw_fac_off(row, cofsA, n));
-                if (rt == cA) a[1] = 0u;                 // upper 8 x 8 block of the diagonal tile
-                mma_f16_16816(dA, a, b0, b1);
-            }
-            if (onB && rt >= cB) {
-                uint32_t a[4];
-                ldsm_x4_trans(a, X + 2u * (uint32_t)sw_fac_off(row, cofsB, n));
-                if (rt == cB) a[1] = 0u;
-                mma_f16_16816(dB, a, b0, b1);
-            }
+        switch (warp) {
+            case 0: sw_cols<0, 7>(X, ntile, lane, hbw, lb, rowtab, dA, dB); break;
+            case 1: sw_cols<1, 6>(X, ntile, lane, hbw, lb, rowtab, dA, dB); break;
+            case 2: sw_cols<2, 5>(X, ntile, lane, hbw, lb, rowtab, dA, dB); break;
+            default: sw_cols<3, 4>(X, ntile, lane, hbw, lb, rowtab, dA, dB); break;
         }
-        if (t == 0) {
+        if (tq == 0) {
             // s is no longer read (it was split into hb before the first barrier)
-            if (onA) {
+            const int cA = warp, cB = 7 - warp;
+            if (cA < ntile) {
                 const int c0 = 16 * cA + g, c1 = c0 + 8;
-                if (c0 < n) s[c0] = (dA[0] + dA[1]) * inv;
-                if (c1 < n) s[c1] = (dA[2] + dA[3]) * inv;
+                s[c0] = (dA[0] + dA[1]) * inv;
+                s[c1] = (dA[2] + dA[3]) * inv;
             }
-            if (onB) {
+            if (cB <= 6 && cB < ntile) {
                 const int c0 = 16 * cB + g, c1 = c0 + 8;
-                if (c0 < n) s[c0] = (dB[0] + dB[1]) * inv;
-                if (c1 < n) s[c1] = (dB[2] + dB[3]) * inv;
+                s[c0] = (dB[0] + dB[1]) * inv;
+                s[c1] = (dB[2] + dB[3]) * inv;
             }
         }
     }
