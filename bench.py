@@ -531,7 +531,8 @@ def oracle_pcg_count(n):
             elif line.strip():
                 f = line.split()
                 rows[int(f[0])] = dict(iterations=int(f[1]), rel_residual=float(f[2]), build_s=float(f[3]),
-                                       solve_s=float(f[4]), ms_per_iteration=float(f[5]), active=int(f[6]))
+                                       solve_s=float(f[4]), ms_per_iteration=float(f[5]), active=int(f[6]),
+                                       blas_threads=int(f[7]) if len(f) > 7 else None)
     return rows.get(n, {}).get("iterations"), {"rows": rows, "header": head}
 
 
