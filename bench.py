@@ -597,28 +597,90 @@ def host_cpu():
     return model, os.cpu_count()
 
 
+BLAS_ENV = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+
+
+def _capped_child(conn, fn, args):
+    try:
+        conn.send(("ok", fn(*args)))
+    except BaseException as e:  # reported to the parent
+        conn.send(("error", repr(e)))
+    conn.close()
+
+
+def run_blas_capped(fn, *args, threads=None):
+    """fn(*args) with numpy's BLAS pool capped at ``threads`` (None: the
+    default pool).  With threadpoolctl the cap is set in this process;
+    where it is not installed, fn runs in a spawned process started with
+    the BLAS thread variables set (spawned, not forked: this process may
+    hold a CUDA context).  Returns (result, how the cap was set)."""
+    if threads is None:
+        return fn(*args), "default pool"
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:
+        threadpool_limits = None
+    if threadpool_limits is not None:
+        with threadpool_limits(limits=threads):
+            return fn(*args), "threadpoolctl"
+    import multiprocessing as mp
+    old = {k: os.environ.get(k) for k in BLAS_ENV}
+    try:
+        for k in BLAS_ENV:
+            os.environ[k] = str(threads)
+        ctx = mp.get_context("spawn")
+        parent, child = ctx.Pipe(duplex=False)
+        proc = ctx.Process(target=_capped_child, args=(child, fn, args))
+        proc.start()
+        child.close()
+        try:
+            kind, res = parent.recv()      # EOFError if the child died before sending
+        finally:
+            proc.join()
+        if kind != "ok":
+            raise RuntimeError(f"capped oracle run failed: {res}")
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return res, "spawned process, BLAS thread variables set"
+
+
+def _pcg_iteration_sample(A, b, budget_s):
+    """Seconds per oracle Jacobi-PCG iteration: 5 iterations to size the
+    sample, then as many as fit in budget_s (5..400)."""
+    from oracle import solve as So
+    k = 5
+    t_it = So.time_pcg_iterations(A, b, k) / k
+    k2 = int(max(5, min(400, budget_s / max(t_it, 1e-6))))
+    return So.time_pcg_iterations(A, b, k2) / k2, k2
+
+
+def _timed_pcg(A, b, tol):
+    from oracle import solve as So
+    t0 = time.perf_counter()
+    _, it, rel = So.pcg(A, b, tol=tol, max_iter=10 ** 7)
+    return (time.perf_counter() - t0) * 1e3, it, rel
+
+
 def cpu_sample(wl, n_iter, budget_s=8.0, count_source="", threads=None, S=None):
     """Time the oracle as it stands on host cores: the system build
     (fractions, validity, explicit CSR assembly, right-hand side) once, a
     bounded number of its Jacobi-PCG iterations, one recovery; extrapolate to
     ``n_iter`` iterations.  ``threads`` caps numpy's BLAS pool (None: the
     default pool; scipy's sparse product runs on one thread either way)."""
-    from threadpoolctl import threadpool_limits
-    from oracle import solve as So
     from oracle import system as S_
     t_build = None
     if S is None:
         t0 = time.perf_counter()
         S = S_.build_system(S_.StokesInput(**wl.as_oracle_kwargs()))
         t_build = time.perf_counter() - t0
-    with threadpool_limits(limits=threads):
-        k = 5
-        t_it = So.time_pcg_iterations(S.A, S.b, k) / k
-        k2 = int(max(5, min(400, budget_s / max(t_it, 1e-6))))
-        t_it = So.time_pcg_iterations(S.A, S.b, k2) / k2
-        t0 = time.perf_counter()
-        S_.recover_velocity(S, np.zeros(S.A.shape[0]))
-        t_rec = time.perf_counter() - t0
+    (t_it, k2), _ = run_blas_capped(_pcg_iteration_sample, S.A, S.b, budget_s, threads=threads)
+    t0 = time.perf_counter()
+    S_.recover_velocity(S, np.zeros(S.A.shape[0]))
+    t_rec = time.perf_counter() - t0
     return S, t_build, t_it, t_rec, k2
 
 
@@ -794,18 +856,14 @@ def run_reference(args):
     # complete oracle solves on this host: config 1 (32^2 disk, FP64 PCG to
     # 1e-10) and the bump workload at a small size (to 1e-8), on all cores
     # and on one
-    from threadpoolctl import threadpool_limits
     complete = {}
     nb = args.ref_complete_size
     for label, wlc, tol in (("disk32_config1", W.disk_in_box(32, seed=1), 1e-10),
                             (f"bumps{nb}", W.bumps_2d(nb, seed=2), 1e-8)):
         Sc = S_.build_system(S_.StokesInput(**wlc.as_oracle_kwargs()))
         for th_name, th in (("all_cores", None), ("one_thread", 1)):
-            with threadpool_limits(limits=th):
-                t0 = time.perf_counter()
-                _, it, rel = So.pcg(Sc.A, Sc.b, tol=tol, max_iter=10 ** 7)
-                complete[f"{label}_{th_name}"] = {"ms": (time.perf_counter() - t0) * 1e3, "iterations": it,
-                                                  "rel_residual": rel}
+            (ms, it, rel), how = run_blas_capped(_timed_pcg, Sc.A, Sc.b, tol, threads=th)
+            complete[f"{label}_{th_name}"] = {"ms": ms, "iterations": it, "rel_residual": rel, "threads": how}
     sample = (f"oracle build ({t_build:.1f} s, once) + per step a bounded sample of its FP64 Jacobi-PCG iterations "
               f"on the full {n}^2 system ({np.mean(per_it) * 1e3:.2f} ms each), extrapolated to the oracle's own "
               f"{n_it} iterations to 1e-8 (tests/golden/oracle_pcg_counts.txt); numpy's default BLAS pool on "

@@ -1,4 +1,5 @@
 // C-ABI entry points of libstokes (declared in include/stokes.h).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -186,6 +187,8 @@ stokes_status stokes_create(stokes_ctx* out, const stokes_grid* g, void* stream)
     size_t oM64 = add(sizeof(double) * S * c.nf), oM32 = add(sizeof(float) * S * c.nf);
     size_t oTF = add(c.ntiles_all);
     size_t oTF4 = add(g->dim == 2 ? (size_t)L.ntx * (L.R / 4) : 1);
+    c.nunits_all = g->dim == 3 ? L.ntx * units_y(L.nty) * units_z(L.ntz) : 0;
+    size_t oUM = add(std::max(c.nunits_all, 1));
     c.weight_bytes = wb;
     cudaError_t e = dalloc(c, &c.weight_block, wb);
     char* base = (char*)c.weight_block;
@@ -210,10 +213,13 @@ stokes_status stokes_create(stokes_ctx* out, const stokes_grid* g, void* stream)
         A.minv32 = (float*)(base + oM32);
         A.tile_flag = (uint8_t*)(base + oTF);
         A.tile_flag4 = (uint8_t*)(base + oTF4);
+        A.unit_mask = (uint8_t*)(base + oUM);
     }
     const int64_t V = (int64_t)c.nf * S;
     if (e == cudaSuccess) e = dalloc(c, (void**)&c.tiles, sizeof(int) * c.ntiles_all);
     if (e == cudaSuccess) e = dalloc(c, (void**)&c.d_ntiles, sizeof(int));
+    if (e == cudaSuccess) e = dalloc(c, (void**)&c.units, sizeof(int) * std::max(c.nunits_all, 1));
+    if (e == cudaSuccess) e = dalloc(c, (void**)&c.d_nunits, sizeof(int));
     if (e == cudaSuccess) e = dalloc(c, (void**)&c.sc, 2 * sizeof(CgScalars));
     if (e == cudaSuccess) e = dalloc(c, (void**)&c.partial, sizeof(double) * 2 * (c.ntiles_all + 32));
     if (e == cudaSuccess) e = dalloc(c, (void**)&c.counter, sizeof(unsigned) * 4);

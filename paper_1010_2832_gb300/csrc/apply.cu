@@ -231,149 +231,220 @@ __global__ void __launch_bounds__(256, MINB) k_apply2d(Layout L, const int* __re
 //   y_txy = d_xy txy + a_xy [z_u(r) - z_u(r-1) + z_v(c) - z_v(c-1)]
 //   y_txz = d_xz txz + a_xz [z_u(q) - z_u(q-1) + z_w(c) - z_w(c-1)]
 //   y_tyz = d_yz tyz + a_yz [z_v(q) - z_v(q-1) + z_w(r) - z_w(r-1)]
-// Staged values; the face values z_u, z_v, z_w are written over U, V, W once
-// every face has been formed (held in registers meanwhile), which keeps the
-// shared memory at six staged arrays (6 CTAs per SM for FP32 instead of 5).
+//
+// The kernel streams along z: a CTA (256 threads) owns a unit of 32 x 8
+// slots and 16 planes and walks its planes in order, keeping two staged
+// planes (34 x 10 positions) and two planes of each face direction in
+// shared memory.  Every staged value is loaded once per unit (halo 1.33x in
+// x and y, 1.13x in z), against 2.4 staged positions per output for a
+// 32 x 4 x 4 tile holding all its planes at once (FP32 on a 256^3 box: 0.63
+// of the measured HBM bandwidth against 0.49).  Issuing a plane's own-value
+// and coefficient loads before its staging (one memory round trip per
+// plane, 64 registers, 4 CTAs per SM) measured 0.63 for FP32 and lost for
+// BF16 coefficients (0.47 against 0.57) and FP64; 8 CTAs per SM at 32
+// registers lost too (0.58).  For output plane q the step
+//   1. stages plane q+1 (in CG mode p = z + beta p_old, written to p_new on
+//      the unit's own slots of active tiles),
+//   2. forms z_u(q), z_v(q) (staged planes q, q+1) and z_w(q+1) (planes q,
+//      q+1),
+//   3. writes y on plane q from z_u(q-1..q), z_v(q-1..q), z_w(q..q+1) and the
+//      own values (re-read from p_new, or x), for slots of active tiles.
 template <class T> struct Smem3 {
-    static constexpr int SX = TX + 2, SY = TY3 + 2, SZ = TZ3 + 2, NS = SX * SY * SZ;
-    static constexpr int ZX = TX + 1, ZY = TY3 + 1, ZZ = TZ3 + 1, NZ = ZX * ZY * ZZ;
-    static constexpr int ZPT = (NZ + 255) / 256;      // face positions per thread
-    static_assert(NZ <= NS, "faces are stored over the staged arrays");
-    T U[NS], V[NS], W[NS], Nxy[NS], Nxz[NS], Nyz[NS];
+    static constexpr int SX = TX + 2, SY = UY3 + 2, NS = SX * SY;   // staged plane: 34 x 10
+    static constexpr int FX = TX + 1, FY = UY3 + 1, NF = FX * FY;   // faces per plane: 33 x 9
+    T st[2][6][NS];        // staged planes by parity: U, V, W, Nxy, Nxz, Nyz
+    T fz[3][2][NF];        // z_u, z_v, z_w by plane parity
 };
 
 template <class T, class C, int MODE>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) k_apply3d(Layout L, const int* __restrict__ tiles, Coef<C> cf,
-                                                 const T* __restrict__ x, T* __restrict__ y, ApplyArgs args,
-                                                 int ntiles) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) k_apply3d(Layout L, Coef<C> cf, const T* __restrict__ x,
+                                                                          T* __restrict__ y, ApplyArgs args) {
     using SM = Smem3<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SM& sm = *reinterpret_cast<SM*>(smem_raw);
     if (MODE == MODE_CG && args.sc->done) return;
-    Acc<T> acc;
-    // persistent over the tile list: one block reduction per CTA, not per tile
-    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
-    const int tile = tiles ? tiles[k] : k;
-    const int tcx = tile % L.ntx, trest = tile / L.ntx;
-    const int c0 = tcx * TX, r0 = (trest % L.nty) * TY3, q0 = (trest / L.nty) * TZ3;
+    const int t = threadIdx.x;
+    const int nuy = units_y(L.nty);
+    const int u = args.units ? args.units[blockIdx.x] : blockIdx.x;
+    unsigned mask;
+    const int ux = u % L.ntx, urest = u / L.ntx, uy = urest % nuy, uz = urest / nuy;
+    if (args.umask) {
+        mask = args.umask[u];
+    } else {                                  // every tile of the grid
+        mask = 0;
+        for (int dz = 0; dz < 4; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                if (2 * uy + dy < L.nty && 4 * uz + dz < L.ntz) mask |= 1u << (dy + 2 * dz);
+    }
+    const int c0 = ux * TX, r0 = uy * UY3, q0 = uz * UZ3;
     const int64_t S = L.stride;
     const C *a_c = cf.f[0], *a_xy = cf.f[1], *a_xz = cf.f[2], *a_yz = cf.f[3];
     const C *d_c = cf.f[4], *d_xy = cf.f[5], *d_xz = cf.f[6], *d_yz = cf.f[7];
     const C *K_u = cf.f[8], *K_v = cf.f[9], *K_w = cf.f[10];
     const T* pold = (const T*)args.pold;
     T* pnew = (T*)args.pnew;
-    T beta = MODE == MODE_CG ? (T)args.sc->beta : T(0);
-    const int t = threadIdx.x;
-    // unknown fields: 0 txx, 1 tyy, 2 txy, 3 txz, 4 tyz, 5 p
-    for (int e = t; e < SM::NS; e += 256) {
-        int ii = e % SM::SX, rest = e / SM::SX, jj = rest % SM::SY, kk = rest / SM::SY;
-        int64_t o = L.off(c0 - 1 + ii, r0 - 1 + jj, q0 - 1 + kk);
-        T v[6];
+    const T beta = MODE == MODE_CG ? (T)args.sc->beta : T(0);
+    // whether slot row r (padded) of plane q belongs to an active tile of the unit
+    auto active = [&](int r, int q) -> bool {
+        const int dy = (r - r0) / TY3, dz = (q - q0) / TZ3;
+        return (mask >> (dy + 2 * dz)) & 1u;
+    };
+    // unknown fields: 0 txx, 1 tyy, 2 txy, 3 txz, 4 tyz, 5 p.  Staged rows past
+    // the padded rows (row R is the next plane's pad row; later rows are only
+    // read for the outputs and faces of inactive tile rows past the grid)
+    // are zero, so every read stays inside the guards.
+    auto stage = [&](int q) {
+        T(*st)[SM::NS] = sm.st[q & 1];
+        const bool own_plane = q >= q0 && q < q0 + UZ3;
+        for (int e = t; e < SM::NS; e += 256) {
+            const int ii = e % SM::SX, jj = e / SM::SX;
+            if (r0 - 1 + jj > L.R) {
 #pragma unroll
-        for (int f = 0; f < 6; ++f) v[f] = stage_val<T, MODE>(x + f * S, pold + f * S, beta, o);
-        if (MODE == MODE_CG && ii >= 1 && ii <= TX && jj >= 1 && jj <= TY3 && kk >= 1 && kk <= TZ3) {
+                for (int f = 0; f < 6; ++f) st[f][e] = T(0);
+                continue;
+            }
+            const int64_t o = L.off(c0 - 1 + ii, r0 - 1 + jj, q);
+            T v[6];
 #pragma unroll
-            for (int f = 0; f < 6; ++f) pnew[f * S + o] = v[f];
+            for (int f = 0; f < 6; ++f) v[f] = stage_val<T, MODE>(x + f * S, pold + f * S, beta, o);
+            if (MODE == MODE_CG && own_plane && ii >= 1 && ii <= TX && jj >= 1 && jj <= UY3 &&
+                active(r0 - 1 + jj, q)) {
+#pragma unroll
+                for (int f = 0; f < 6; ++f) pnew[f * S + o] = v[f];
+            }
+            const T ac = ld<T, C>(a_c, o);
+            st[0][e] = ac * (v[5] - v[0]);
+            st[1][e] = ac * (v[5] - v[1]);
+            st[2][e] = ac * (v[5] + v[0] + v[1]);
+            st[3][e] = ld<T, C>(a_xy, o) * v[2];
+            st[4][e] = ld<T, C>(a_xz, o) * v[3];
+            st[5][e] = ld<T, C>(a_yz, o) * v[4];
         }
-        T ac = ld<T, C>(a_c, o);
-        sm.U[e] = ac * (v[5] - v[0]);
-        sm.V[e] = ac * (v[5] - v[1]);
-        sm.W[e] = ac * (v[5] + v[0] + v[1]);
-        sm.Nxy[e] = ld<T, C>(a_xy, o) * v[2];
-        sm.Nxz[e] = ld<T, C>(a_xz, o) * v[3];
-        sm.Nyz[e] = ld<T, C>(a_yz, o) * v[4];
-    }
+    };
+    // face coefficients of z_u(q), z_v(q), z_w(q+1) at face position e (zero
+    // past the padded rows, see stage)
+    constexpr int FPT = (SM::NF + 255) / 256;     // face positions per thread (2)
+    auto face_k = [&](int q, T (&k)[FPT][3]) {
+#pragma unroll
+        for (int it = 0; it < FPT; ++it) {
+            const int e = t + 256 * it;
+            k[it][0] = k[it][1] = k[it][2] = T(0);
+            if (e < SM::NF) {
+                const int ii = e % SM::FX, jj = e / SM::FX;
+                if (r0 + jj <= L.R) {
+                    k[it][0] = ld<T, C>(K_u, L.off(c0 + ii, r0 - 1 + jj, q));
+                    k[it][1] = ld<T, C>(K_v, L.off(c0 - 1 + ii, r0 + jj, q));
+                    k[it][2] = ld<T, C>(K_w, L.off(c0 - 1 + ii, r0 - 1 + jj, q + 1));
+                }
+            }
+        }
+    };
+    // z_u(q), z_v(q) from staged planes q and q+1; z_w(q+1) from planes q and q+1
+    auto faces = [&](int q, const T (&k)[FPT][3]) {
+        const T(*A)[SM::NS] = sm.st[q & 1];
+        const T(*B)[SM::NS] = sm.st[(q + 1) & 1];
+#pragma unroll
+        for (int it = 0; it < FPT; ++it) {
+            const int e = t + 256 * it;
+            if (e >= SM::NF) break;
+            const int ii = e % SM::FX, jj = e / SM::FX;
+            if (r0 + jj > L.R) {
+                sm.fz[0][q & 1][e] = sm.fz[1][q & 1][e] = sm.fz[2][(q + 1) & 1][e] = T(0);
+                continue;
+            }
+            // z_u at (c0+ii, r0-1+jj, q): staged (ii+1, jj)
+            const int su = jj * SM::SX + ii + 1;
+            sm.fz[0][q & 1][e] = k[it][0] * ((A[0][su] - A[0][su - 1]) + (A[3][su] - A[3][su + SM::SX]) +
+                                             (A[4][su] - B[4][su]));
+            // z_v at (c0-1+ii, r0+jj, q): staged (ii, jj+1)
+            const int sv = (jj + 1) * SM::SX + ii;
+            sm.fz[1][q & 1][e] = k[it][1] * ((A[1][sv] - A[1][sv - SM::SX]) + (A[3][sv] - A[3][sv + 1]) +
+                                             (A[5][sv] - B[5][sv]));
+            // z_w at (c0-1+ii, r0-1+jj, q+1): staged (ii, jj) of planes q+1 and q
+            const int sw = jj * SM::SX + ii;
+            sm.fz[2][(q + 1) & 1][e] = k[it][2] * ((B[2][sw] - A[2][sw]) + (B[4][sw] - B[4][sw + 1]) +
+                                                   (B[5][sw] - B[5][sw + SM::SX]));
+        }
+    };
+    Acc<T> acc;
+    // planes up to the last tile layer holding an active tile (all inside
+    // the padded planes: staging reaches plane q_end <= Q, the trailing pad)
+    int dz_end = 0;
+    for (int dz = 0; dz < 4; ++dz)
+        if ((mask >> (2 * dz)) & 3u) dz_end = dz + 1;
+    const int q_end = q0 + TZ3 * dz_end;
+    if (q_end > q0) {
+    // prologue: planes q0-1 and q0; z_u(q0-1), z_v(q0-1); z_w(q0)
+    stage(q0 - 1);
+    stage(q0);
     __syncthreads();
-    // staged index of (c, r, q) relative to (c0-1, r0-1, q0-1)
-    auto si = [](int ii, int jj, int kk) { return (kk * SM::SY + jj) * SM::SX + ii; };
-    T fzu[SM::ZPT], fzv[SM::ZPT], fzw[SM::ZPT];
-#pragma unroll
-    for (int it = 0; it < SM::ZPT; ++it) {
-        const int e = t + 256 * it;
-        if (e >= SM::NZ) break;
-        int ii = e % SM::ZX, rest = e / SM::ZX, jj = rest % SM::ZY, kk = rest / SM::ZY;
-        // z_u at (c0+ii, r0-1+jj, q0-1+kk): staged coords (ii+1, jj, kk)
-        {
-            int s = si(ii + 1, jj, kk);
-            T ku = ld<T, C>(K_u, L.off(c0 + ii, r0 - 1 + jj, q0 - 1 + kk));
-            fzu[it] = ku * ((sm.U[s] - sm.U[s - 1]) + (sm.Nxy[s] - sm.Nxy[s + SM::SX]) +
-                            (sm.Nxz[s] - sm.Nxz[s + SM::SX * SM::SY]));
-        }
-        // z_v at (c0-1+ii, r0+jj, q0-1+kk): staged (ii, jj+1, kk)
-        {
-            int s = si(ii, jj + 1, kk);
-            T kv = ld<T, C>(K_v, L.off(c0 - 1 + ii, r0 + jj, q0 - 1 + kk));
-            fzv[it] = kv * ((sm.V[s] - sm.V[s - SM::SX]) + (sm.Nxy[s] - sm.Nxy[s + 1]) +
-                            (sm.Nyz[s] - sm.Nyz[s + SM::SX * SM::SY]));
-        }
-        // z_w at (c0-1+ii, r0-1+jj, q0+kk): staged (ii, jj, kk+1)
-        {
-            int s = si(ii, jj, kk + 1);
-            T kw = ld<T, C>(K_w, L.off(c0 - 1 + ii, r0 - 1 + jj, q0 + kk));
-            fzw[it] = kw * ((sm.W[s] - sm.W[s - SM::SX * SM::SY]) + (sm.Nxz[s] - sm.Nxz[s + 1]) +
-                            (sm.Nyz[s] - sm.Nyz[s + SM::SX]));
-        }
-    }
-    __syncthreads();                           // every staged value is read: faces go over U, V, W
-    T* const zua = sm.U;
-    T* const zva = sm.V;
-    T* const zwa = sm.W;
-#pragma unroll
-    for (int it = 0; it < SM::ZPT; ++it) {
-        const int e = t + 256 * it;
-        if (e >= SM::NZ) break;
-        zua[e] = fzu[it];
-        zva[e] = fzv[it];
-        zwa[e] = fzw[it];
-    }
+    T k0[FPT][3];
+    face_k(q0 - 1, k0);
+    faces(q0 - 1, k0);
     __syncthreads();
-    auto zi = [](int ii, int jj, int kk) { return (kk * SM::ZY + jj) * SM::ZX + ii; };
-    const int tx = t & (TX - 1);
-    for (int rep = 0; rep < 2; ++rep) {
-        int lin = (t >> 5) + rep * 8;          // 16 rows of 32 per tile
-        int ty = lin % TY3, tz = lin / TY3;
-        int64_t o = L.off(c0 + tx, r0 + ty, q0 + tz);
-        T v[6];
-#pragma unroll
-        for (int f = 0; f < 6; ++f) v[f] = MODE == MODE_CG ? pnew[f * S + o] : x[f * S + o];
-        // z_u(c, r, q): index (tx, ty+1, tz+1); z_u(c+1): (tx+1, ...)
-        T zu = zua[zi(tx, ty + 1, tz + 1)], zu_cp = zua[zi(tx + 1, ty + 1, tz + 1)];
-        T zu_rm = zua[zi(tx, ty, tz + 1)], zu_qm = zua[zi(tx, ty + 1, tz)];
-        // z_v(c, r, q): (tx+1, ty, tz+1)
-        T zv = zva[zi(tx + 1, ty, tz + 1)], zv_rp = zva[zi(tx + 1, ty + 1, tz + 1)];
-        T zv_cm = zva[zi(tx, ty, tz + 1)], zv_qm = zva[zi(tx + 1, ty, tz)];
-        // z_w(c, r, q): (tx+1, ty+1, tz)
-        T zw = zwa[zi(tx + 1, ty + 1, tz)], zw_qp = zwa[zi(tx + 1, ty + 1, tz + 1)];
-        T zw_cm = zwa[zi(tx, ty + 1, tz)], zw_rm = zwa[zi(tx + 1, ty, tz)];
-        T ac = ld<T, C>(a_c, o), dc = ld<T, C>(d_c, o);
-        T yv[6];
-        if (ac != T(0)) {
-            T ww = zw - zw_qp;
-            yv[5] = ac * ((zu - zu_cp) + (zv - zv_rp) + ww);
-            yv[0] = dc * (v[0] + T(0.5) * v[1]) + ac * ((zu_cp - zu) + ww);
-            yv[1] = dc * (v[1] + T(0.5) * v[0]) + ac * ((zv_rp - zv) + ww);
-        } else {
-            yv[5] = v[5]; yv[0] = v[0]; yv[1] = v[1];
-        }
-        yv[2] = ld<T, C>(d_xy, o) * v[2] + ld<T, C>(a_xy, o) * ((zu - zu_rm) + (zv - zv_cm));
-        yv[3] = ld<T, C>(d_xz, o) * v[3] + ld<T, C>(a_xz, o) * ((zu - zu_qm) + (zw - zw_cm));
-        yv[4] = ld<T, C>(d_yz, o) * v[4] + ld<T, C>(a_yz, o) * ((zv - zv_qm) + (zw - zw_rm));
-        if (MODE == MODE_RESID) {
-            const T* b = (const T*)args.b;
-#pragma unroll
-            for (int f = 0; f < 6; ++f) yv[f] = b[f * S + o] - yv[f];
-        }
-#pragma unroll
-        for (int f = 0; f < 6; ++f) y[f * S + o] = yv[f];
-        if (MODE == MODE_RESID) {
-#pragma unroll
-            for (int f = 0; f < 6; ++f) acc.add(yv[f], yv[f]);
-        } else if (MODE == MODE_CG) {
-#pragma unroll
-            for (int f = 0; f < 6; ++f) acc.add(v[f], yv[f]);
-        }
     }
-    __syncthreads();                           // shared memory is reused by the next tile
+    const int tx = t & (TX - 1), ty = t >> 5;
+    auto fi = [](int ii, int jj) { return jj * SM::FX + ii; };
+    for (int q = q0; q < q_end; ++q) {
+        stage(q + 1);
+        __syncthreads();
+        {
+            T kq[FPT][3];
+            face_k(q, kq);
+            faces(q, kq);
+        }
+        __syncthreads();
+        const int r = r0 + ty;
+        if (active(r, q)) {
+            const int64_t o = L.off(c0 + tx, r, q);
+            T v[6];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) v[f] = MODE == MODE_CG ? pnew[f * S + o] : x[f * S + o];
+            const T* zu_q = sm.fz[0][q & 1];
+            const T* zu_m = sm.fz[0][(q - 1) & 1];
+            const T* zv_q = sm.fz[1][q & 1];
+            const T* zv_m = sm.fz[1][(q - 1) & 1];
+            const T* zw_q = sm.fz[2][q & 1];
+            const T* zw_p = sm.fz[2][(q + 1) & 1];
+            // z_u(c, r, q): face (tx, ty+1); z_v(c, r, q): (tx+1, ty); z_w(c, r, q): (tx+1, ty+1)
+            const T zu = zu_q[fi(tx, ty + 1)], zu_cp = zu_q[fi(tx + 1, ty + 1)];
+            const T zu_rm = zu_q[fi(tx, ty)], zu_qm = zu_m[fi(tx, ty + 1)];
+            const T zv = zv_q[fi(tx + 1, ty)], zv_rp = zv_q[fi(tx + 1, ty + 1)];
+            const T zv_cm = zv_q[fi(tx, ty)], zv_qm = zv_m[fi(tx + 1, ty)];
+            const T zw = zw_q[fi(tx + 1, ty + 1)], zw_qp = zw_p[fi(tx + 1, ty + 1)];
+            const T zw_cm = zw_q[fi(tx, ty + 1)], zw_rm = zw_q[fi(tx + 1, ty)];
+            const T ac = ld<T, C>(a_c, o), dc = ld<T, C>(d_c, o);
+            T yv[6];
+            if (ac != T(0)) {
+                const T ww = zw - zw_qp;
+                yv[5] = ac * ((zu - zu_cp) + (zv - zv_rp) + ww);
+                yv[0] = dc * (v[0] + T(0.5) * v[1]) + ac * ((zu_cp - zu) + ww);
+                yv[1] = dc * (v[1] + T(0.5) * v[0]) + ac * ((zv_rp - zv) + ww);
+            } else {
+                yv[5] = v[5]; yv[0] = v[0]; yv[1] = v[1];
+            }
+            yv[2] = ld<T, C>(d_xy, o) * v[2] + ld<T, C>(a_xy, o) * ((zu - zu_rm) + (zv - zv_cm));
+            yv[3] = ld<T, C>(d_xz, o) * v[3] + ld<T, C>(a_xz, o) * ((zu - zu_qm) + (zw - zw_cm));
+            yv[4] = ld<T, C>(d_yz, o) * v[4] + ld<T, C>(a_yz, o) * ((zv - zv_qm) + (zw - zw_rm));
+            if (MODE == MODE_RESID) {
+                const T* b = (const T*)args.b;
+#pragma unroll
+                for (int f = 0; f < 6; ++f) yv[f] = b[f * S + o] - yv[f];
+            }
+#pragma unroll
+            for (int f = 0; f < 6; ++f) y[f * S + o] = yv[f];
+            if (MODE == MODE_RESID) {
+#pragma unroll
+                for (int f = 0; f < 6; ++f) acc.add(yv[f], yv[f]);
+            } else if (MODE == MODE_CG) {
+#pragma unroll
+                for (int f = 0; f < 6; ++f) acc.add(v[f], yv[f]);
+            }
+        }
+        // the next step's staging overwrites the staged plane q (read by the
+        // faces above, before the barrier); its faces overwrite z_u(q-1),
+        // z_v(q-1) and z_w(q), read here: the barrier after its staging
+        // orders them
     }
     if (MODE != MODE_PLAIN) {
         double v = acc.warp();
@@ -418,11 +489,12 @@ static cudaError_t launch_mode(const Layout& L, const int* tiles, int ntiles, co
         const int grid = std::min(ntiles, resident_ctas((const void*)k_apply2d<T, C, MODE, MINB>, 256, 0, cache2));
         k_apply2d<T, C, MODE, MINB><<<grid, 256, 0, s>>>(L, tiles, cf, x, y, a, ntiles);
     } else {
-        // 3D: one tile per CTA measured faster than the persistent loop
-        // (the staging buffers are large, so fewer CTAs fit per SM)
-        size_t sm = sizeof(Smem3<T>);
+        // 3D: one CTA per unit (32 x 8 slots, 16 planes), over the active
+        // units (an apply over the active tiles needs the unit list) or all
         (void)cache3;
-        k_apply3d<T, C, MODE><<<ntiles, 256, sm, s>>>(L, tiles, cf, x, y, a, ntiles);
+        if (tiles && !a.units) return cudaErrorInvalidValue;
+        const int nu = tiles ? a.nunits : L.ntx * units_y(L.nty) * units_z(L.ntz);
+        if (nu > 0) k_apply3d<T, C, MODE><<<nu, 256, sizeof(Smem3<T>), s>>>(L, cf, x, y, a);
     }
     return cudaGetLastError();
 }

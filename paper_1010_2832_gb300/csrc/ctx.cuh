@@ -26,6 +26,7 @@ struct DevArrays {
     float* minv32;
     uint8_t* tile_flag;
     uint8_t* tile_flag4;  // 2D: activity of 32 x 4 tiles (batched solver plans)
+    uint8_t* unit_mask;   // 3D: active tiles of each apply unit (bit mask, see UY3)
 };
 
 // Learned-preconditioner state of a context (fpcg.cu).
@@ -60,6 +61,10 @@ struct Ctx {
     int ntiles_active = 0;
     int* tiles = nullptr;       // active tile list (device)
     int* d_ntiles = nullptr;
+    int nunits_all = 0;         // 3D apply units of the grid
+    int nunits_active = 0;
+    int* units = nullptr;       // active unit list (device, 3D)
+    int* d_nunits = nullptr;
     bool have_weights = false;
     double min_face_liquid = 0.0;   // floor of the live faces' mass fraction (next weight build)
     bool own_stream = false;
@@ -93,6 +98,14 @@ struct Ctx {
     void* adv_scratch = nullptr;
 
     DevArrays dev_arrays() const { return A; }
+    // arguments of an apply over the active tiles (3D: the active units)
+    ApplyArgs apply_args() const {
+        ApplyArgs a{};
+        a.units = units;
+        a.umask = A.unit_mask;
+        a.nunits = nunits_active;
+        return a;
+    }
     cudaError_t zero_weights() { return cudaMemsetAsync(weight_block, 0, weight_bytes, stream); }
     template <class C> Coef<C> coef() const;
     int64_t vec_elems() const { return (int64_t)nf * L.stride; }

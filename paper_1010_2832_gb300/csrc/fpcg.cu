@@ -275,7 +275,7 @@ cudaError_t run_inner_fpcg(Ctx* c, stokes_net_s* net, double scale, double tol_r
     while (it < max_iter && rr > tol2 && rr0 > 0) {
         // p = z + beta p_old, q = A p, alpha = rz / p.q
         cudaMemcpyAsync(c->sc, &hs, sizeof(CgScalars), cudaMemcpyHostToDevice, s);
-        ApplyArgs a{};
+        ApplyArgs a = c->apply_args();
         a.pold = w.p[it & 1];
         a.pnew = w.p[(it & 1) ^ 1];
         a.partial = c->partial;

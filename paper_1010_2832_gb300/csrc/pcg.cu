@@ -361,7 +361,7 @@ static void schwarz_body(Ctx* c, cudaStream_t s, cudaGraphConditionalHandle h, i
     const Layout& L = c->L;
     const int nb = c->ntiles_active;
     CgWork<float>& w = c->w32;
-    ApplyArgs a{};
+    ApplyArgs a = c->apply_args();
     a.pold = w.p[parity];
     a.pnew = w.p[parity ^ 1];
     a.partial = c->partial;
@@ -463,7 +463,7 @@ static cudaError_t build_inner_graph(Ctx* c, CgWork<T>& w, const T* minv, const 
     if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
         return e;
     for (int k = 0; k < 2; ++k) {
-        ApplyArgs a{};
+        ApplyArgs a = c->apply_args();
         a.pold = w.p[k];
         a.pnew = w.p[k ^ 1];
         a.partial = part;
@@ -508,7 +508,7 @@ static cudaError_t run_inner(Ctx* c, int prec_slot, CgWork<T>& w, const T* minv,
     chunk = chunk < 2 ? 2 : (chunk + 1) & ~1;   // even: p[0]/p[1] parity restarts each chunk
     for (long it = 0;; it += chunk) {
         for (int k = 0; k < chunk; ++k) {
-            ApplyArgs a{};
+            ApplyArgs a = c->apply_args();
             a.pold = w.p[k & 1];
             a.pnew = w.p[(k & 1) ^ 1];
             a.partial = c->partial;
@@ -638,7 +638,7 @@ stokes_status solve_system(Ctx* c, const double* b, double* x, const stokes_opti
     double rr = bb;
     int mode = o->mode;
     const int use_graph = o->use_graph;
-    ApplyArgs ra{};
+    ApplyArgs ra = c->apply_args();
     ra.b = b;
     ra.partial = c->partial;
     ra.counter = c->counter;
@@ -891,7 +891,7 @@ static cudaError_t bench_impl(Ctx* c, CgWork<T>& w, const T* minv, const Coef<C>
     // two untimed iterations first: the first launch of a kernel in a process
     // can wait on the host (module loading), which the events would count
     for (int k = -2; k < 0; ++k) {
-        ApplyArgs a{};
+        ApplyArgs a = c->apply_args();
         a.pold = w.p[k & 1];
         a.pnew = w.p[(k & 1) ^ 1];
         a.partial = c->partial;
@@ -905,7 +905,7 @@ static cudaError_t bench_impl(Ctx* c, CgWork<T>& w, const T* minv, const Coef<C>
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     cudaEventRecord(ev[0], s);
     for (int k = 0; k < launches; ++k) {
-        ApplyArgs a{};
+        ApplyArgs a = c->apply_args();
         a.pold = w.p[k & 1];
         a.pnew = w.p[(k & 1) ^ 1];
         a.partial = c->partial;

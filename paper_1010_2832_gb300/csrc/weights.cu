@@ -610,6 +610,22 @@ __global__ void k_finish3d(Layout L, DevArrays D) {
     }
 }
 
+// Tile mask of every 3D apply unit (32 x 8 x 16 slots: two tile rows, four
+// tile layers; bit dy + 2 dz), tiles past the tile grid counted inactive.
+__global__ void k_unit_masks(Layout L, const uint8_t* __restrict__ tflag, uint8_t* __restrict__ umask, int nunits) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nunits) return;
+    const int nuy = units_y(L.nty);
+    const int ux = u % L.ntx, rest = u / L.ntx, uy = rest % nuy, uz = rest / nuy;
+    unsigned m = 0;
+    for (int dz = 0; dz < 4; ++dz)
+        for (int dy = 0; dy < 2; ++dy) {
+            const int ty = 2 * uy + dy, tz = 4 * uz + dz;
+            if (ty < L.nty && tz < L.ntz && tflag[((int64_t)tz * L.nty + ty) * L.ntx + ux]) m |= 1u << (dy + 2 * dz);
+        }
+    umask[u] = (uint8_t)m;
+}
+
 // Ordered compaction of the tile flags (one block; tile counts are small).
 __global__ void k_compact_tiles(const uint8_t* flag, int n, int* list, int* count) {
     __shared__ int warp_tot[32];
@@ -665,8 +681,15 @@ cudaError_t launch_build_weights(Ctx* c, const double* phiL, const double* phiS,
         k_finish3d<<<grd, blk, 0, s>>>(L, D);
     }
     k_compact_tiles<<<1, 1024, 0, s>>>(D.tile_flag, c->ntiles_all, c->tiles, c->d_ntiles);
+    if (L.dim == 3) {
+        k_unit_masks<<<(c->nunits_all + 255) / 256, 256, 0, s>>>(L, D.tile_flag, D.unit_mask, c->nunits_all);
+        k_compact_tiles<<<1, 1024, 0, s>>>(D.unit_mask, c->nunits_all, c->units, c->d_nunits);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(&c->ntiles_active, c->d_ntiles, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return e;
+    if (L.dim == 3 &&
+        (e = cudaMemcpyAsync(&c->nunits_active, c->d_nunits, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return e;
     return cudaStreamSynchronize(s);
 }

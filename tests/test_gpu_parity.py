@@ -152,13 +152,23 @@ def _step(ctx, dev, mode, tol, **kw):
     return st, u, x
 
 
+def fp64_residual_floor(S, x_ref):
+    """eps ||A| |x|| / ||b||: below this a relative residual computed in FP64
+    is rounding (the componentwise backward-error bound of b - A x); the
+    oracle's own direct solve lands at 0.4-0.8 of it on these cases."""
+    return np.finfo(float).eps * np.linalg.norm(abs(S.A) @ np.abs(x_ref)) / np.linalg.norm(S.b)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_fp64_solve_matches_direct_solve(name):
     wl, S, ctx, dev = setup(name)
-    st, u, x = _step(ctx, dev, 0, 1e-12)
-    assert st.status == 0 and st.rel_residual <= 1e-12
     nulls = S_.pressure_null_vectors(S)
     x_ref = So.solve_direct(S.A, S.b, nulls)
+    # 1e-12, or the FP64 floor where that is higher (8.2e-12 on rand3d_b,
+    # whose direct solve itself has a relative residual of 6.3e-12)
+    tol = max(1e-12, fp64_residual_floor(S, x_ref))
+    st, u, x = _step(ctx, dev, 0, tol)
+    assert st.status == 0 and st.rel_residual <= tol
     u_ref = S_.recover_velocity(S, x_ref)
     lv = S.live
     umax = max(np.abs(u_ref[lv]).max(), 1e-30)
