@@ -187,7 +187,7 @@ stokes_status stokes_create(stokes_ctx* out, const stokes_grid* g, void* stream)
     size_t oM64 = add(sizeof(double) * S * c.nf), oM32 = add(sizeof(float) * S * c.nf);
     size_t oTF = add(c.ntiles_all);
     size_t oTF4 = add(g->dim == 2 ? (size_t)L.ntx * (L.R / 4) : 1);
-    c.nunits_all = g->dim == 3 ? L.ntx * units_y(L.nty) * units_z(L.ntz) : 0;
+    c.nunits_all = g->dim == 3 ? L.ntx * units_y(L.nty) * units_z(L.ntz, 1) : 0;
     size_t oUM = add(std::max(c.nunits_all, 1));
     c.weight_bytes = wb;
     cudaError_t e = dalloc(c, &c.weight_block, wb);

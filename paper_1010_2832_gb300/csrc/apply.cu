@@ -233,7 +233,8 @@ __global__ void __launch_bounds__(256, MINB) k_apply2d(Layout L, const int* __re
 //   y_tyz = d_yz tyz + a_yz [z_v(q) - z_v(q-1) + z_w(r) - z_w(r-1)]
 //
 // The kernel streams along z: a CTA (256 threads) owns a unit of 32 x 8
-// slots and 16 planes and walks its planes in order, keeping two staged
+// slots and zt tile layers (16 planes; 4 where the active tiles are too few
+// to fill the device with deep units) and walks its planes in order, keeping two staged
 // planes (34 x 10 positions) and two planes of each face direction in
 // shared memory.  Every staged value is loaded once per unit (halo 1.33x in
 // x and y, 1.13x in z), against 2.4 staged positions per output for a
@@ -249,6 +250,9 @@ __global__ void __launch_bounds__(256, MINB) k_apply2d(Layout L, const int* __re
 //      q+1),
 //   3. writes y on plane q from z_u(q-1..q), z_v(q-1..q), z_w(q..q+1) and the
 //      own values (re-read from p_new, or x), for slots of active tiles.
+// (On the thin 3D liquid column the 16-plane units were too few: its apply
+// ran slower than with 32 x 4 x 4 tiles until units of one layer were used
+// for sparse grids.)
 template <class T> struct Smem3 {
     static constexpr int SX = TX + 2, SY = UY3 + 2, NS = SX * SY;   // staged plane: 34 x 10
     static constexpr int FX = TX + 1, FY = UY3 + 1, NF = FX * FY;   // faces per plane: 33 x 9
@@ -266,17 +270,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) k_apply3d(Layout 
     const int t = threadIdx.x;
     const int nuy = units_y(L.nty);
     const int u = args.units ? args.units[blockIdx.x] : blockIdx.x;
+    const int zt = args.units ? args.zt : ZT_MAX;   // tile layers per unit
     unsigned mask;
     const int ux = u % L.ntx, urest = u / L.ntx, uy = urest % nuy, uz = urest / nuy;
     if (args.umask) {
         mask = args.umask[u];
     } else {                                  // every tile of the grid
         mask = 0;
-        for (int dz = 0; dz < 4; ++dz)
+        for (int dz = 0; dz < zt; ++dz)
             for (int dy = 0; dy < 2; ++dy)
-                if (2 * uy + dy < L.nty && 4 * uz + dz < L.ntz) mask |= 1u << (dy + 2 * dz);
+                if (2 * uy + dy < L.nty && zt * uz + dz < L.ntz) mask |= 1u << (dy + 2 * dz);
     }
-    const int c0 = ux * TX, r0 = uy * UY3, q0 = uz * UZ3;
+    const int c0 = ux * TX, r0 = uy * UY3, q0 = uz * zt * TZ3;
     const int64_t S = L.stride;
     const C *a_c = cf.f[0], *a_xy = cf.f[1], *a_xz = cf.f[2], *a_yz = cf.f[3];
     const C *d_c = cf.f[4], *d_xy = cf.f[5], *d_xz = cf.f[6], *d_yz = cf.f[7];
@@ -295,7 +300,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) k_apply3d(Layout 
     // are zero, so every read stays inside the guards.
     auto stage = [&](int q) {
         T(*st)[SM::NS] = sm.st[q & 1];
-        const bool own_plane = q >= q0 && q < q0 + UZ3;
+        const bool own_plane = q >= q0 && q < q0 + zt * TZ3;
         for (int e = t; e < SM::NS; e += 256) {
             const int ii = e % SM::SX, jj = e / SM::SX;
             if (r0 - 1 + jj > L.R) {
@@ -370,7 +375,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) k_apply3d(Layout 
     // planes up to the last tile layer holding an active tile (all inside
     // the padded planes: staging reaches plane q_end <= Q, the trailing pad)
     int dz_end = 0;
-    for (int dz = 0; dz < 4; ++dz)
+    for (int dz = 0; dz < zt; ++dz)
         if ((mask >> (2 * dz)) & 3u) dz_end = dz + 1;
     const int q_end = q0 + TZ3 * dz_end;
     if (q_end > q0) {
@@ -493,7 +498,7 @@ static cudaError_t launch_mode(const Layout& L, const int* tiles, int ntiles, co
         // units (an apply over the active tiles needs the unit list) or all
         (void)cache3;
         if (tiles && !a.units) return cudaErrorInvalidValue;
-        const int nu = tiles ? a.nunits : L.ntx * units_y(L.nty) * units_z(L.ntz);
+        const int nu = tiles ? a.nunits : L.ntx * units_y(L.nty) * units_z(L.ntz, ZT_MAX);
         if (nu > 0) k_apply3d<T, C, MODE><<<nu, 256, sizeof(Smem3<T>), s>>>(L, cf, x, y, a);
     }
     return cudaGetLastError();

@@ -61,7 +61,8 @@ struct Ctx {
     int ntiles_active = 0;
     int* tiles = nullptr;       // active tile list (device)
     int* d_ntiles = nullptr;
-    int nunits_all = 0;         // 3D apply units of the grid
+    int nunits_all = 0;         // 3D apply units of the grid at depth 1 (the most there can be)
+    int unit_zt = ZT_MAX;       // depth of the current units (tile layers), chosen at weight build
     int nunits_active = 0;
     int* units = nullptr;       // active unit list (device, 3D)
     int* d_nunits = nullptr;
@@ -104,6 +105,7 @@ struct Ctx {
         a.units = units;
         a.umask = A.unit_mask;
         a.nunits = nunits_active;
+        a.zt = unit_zt;
         return a;
     }
     cudaError_t zero_weights() { return cudaMemsetAsync(weight_block, 0, weight_bytes, stream); }

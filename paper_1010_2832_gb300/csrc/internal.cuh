@@ -27,11 +27,12 @@ struct Layout {
 constexpr int TX = 32;
 constexpr int TY2 = 8;                 // 2D: 32 x 8 slots, one per thread
 constexpr int TY3 = 4, TZ3 = 4;        // 3D: 32 x 4 x 4 slots, 2 per thread
-// 3D apply unit: 32 x 8 slots streamed over 16 planes (2 x 4 tiles of the
-// tile grid), bit dy + 2 dz of its mask for tile (.., 2 uy + dy, 4 uz + dz)
-constexpr int UY3 = 2 * TY3, UZ3 = 4 * TZ3;
+// 3D apply unit: 32 x 8 slots streamed over zt tile layers of 4 planes
+// (2 x zt tiles of the tile grid, zt = 1..4), bit dy + 2 dz of its mask for
+// tile (.., 2 uy + dy, zt uz + dz)
+constexpr int UY3 = 2 * TY3, ZT_MAX = 4;
 __host__ __device__ inline int units_y(int nty) { return (nty + 1) / 2; }
-__host__ __device__ inline int units_z(int ntz) { return (ntz + 3) / 4; }
+__host__ __device__ inline int units_z(int ntz, int zt) { return (ntz + zt - 1) / zt; }
 
 // Face flags (one byte per face).
 enum : uint8_t { F_LIVE = 1, F_BAD = 2, F_INVALID = 4, F_WALL = 8, F_EXISTS = 16 };
@@ -65,10 +66,11 @@ struct ApplyArgs {
     unsigned* counter;
     CgScalars* sc;
     // 3D: the units to apply (nullptr: every unit of the grid, every tile
-    // in the grid active) and their tile masks
+    // in the grid active, ZT_MAX layers deep), their tile masks and depth
     const int* units;
     const uint8_t* umask;
     int nunits;
+    int zt;
 };
 
 struct Ctx;   // defined in api.cu

@@ -3,6 +3,7 @@
 // Section 8, operator coefficients, the Jacobi diagonal and the list of
 // tiles that hold an active unknown.  One thread per slot of the padded
 // vertex lattice; everything in FP64.
+#include <algorithm>
 #include "internal.cuh"
 #include "ctx.cuh"
 
@@ -610,17 +611,18 @@ __global__ void k_finish3d(Layout L, DevArrays D) {
     }
 }
 
-// Tile mask of every 3D apply unit (32 x 8 x 16 slots: two tile rows, four
-// tile layers; bit dy + 2 dz), tiles past the tile grid counted inactive.
-__global__ void k_unit_masks(Layout L, const uint8_t* __restrict__ tflag, uint8_t* __restrict__ umask, int nunits) {
+// Tile mask of every 3D apply unit (32 x 8 slots x zt tile layers; bit
+// dy + 2 dz), tiles past the tile grid counted inactive.
+__global__ void k_unit_masks(Layout L, int zt, const uint8_t* __restrict__ tflag, uint8_t* __restrict__ umask,
+                             int nunits) {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= nunits) return;
     const int nuy = units_y(L.nty);
     const int ux = u % L.ntx, rest = u / L.ntx, uy = rest % nuy, uz = rest / nuy;
     unsigned m = 0;
-    for (int dz = 0; dz < 4; ++dz)
+    for (int dz = 0; dz < zt; ++dz)
         for (int dy = 0; dy < 2; ++dy) {
-            const int ty = 2 * uy + dy, tz = 4 * uz + dz;
+            const int ty = 2 * uy + dy, tz = zt * uz + dz;
             if (ty < L.nty && tz < L.ntz && tflag[((int64_t)tz * L.nty + ty) * L.ntx + ux]) m |= 1u << (dy + 2 * dz);
         }
     umask[u] = (uint8_t)m;
@@ -681,16 +683,27 @@ cudaError_t launch_build_weights(Ctx* c, const double* phiL, const double* phiS,
         k_finish3d<<<grd, blk, 0, s>>>(L, D);
     }
     k_compact_tiles<<<1, 1024, 0, s>>>(D.tile_flag, c->ntiles_all, c->tiles, c->d_ntiles);
-    if (L.dim == 3) {
-        k_unit_masks<<<(c->nunits_all + 255) / 256, 256, 0, s>>>(L, D.tile_flag, D.unit_mask, c->nunits_all);
-        k_compact_tiles<<<1, 1024, 0, s>>>(D.unit_mask, c->nunits_all, c->units, c->d_nunits);
-    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(&c->ntiles_active, c->d_ntiles, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return e;
-    if (L.dim == 3 &&
-        (e = cudaMemcpyAsync(&c->nunits_active, c->d_nunits, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return e;
+    if (L.dim == 3) {
+        // units of 4 tile layers (16 planes) when there are enough of them to
+        // fill the device a few times over, else of one layer: a thin liquid
+        // region has too few deep units to keep every SM busy
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // (deep units hold 2 ZT_MAX tiles; six CTAs per SM; two waves)
+        c->unit_zt = c->ntiles_active >= 2 * (2 * ZT_MAX) * 6 * std::max(sms, 1) ? ZT_MAX : 1;
+        const int nu = L.ntx * units_y(L.nty) * units_z(L.ntz, c->unit_zt);
+        k_unit_masks<<<(nu + 255) / 256, 256, 0, s>>>(L, c->unit_zt, D.tile_flag, D.unit_mask, nu);
+        k_compact_tiles<<<1, 1024, 0, s>>>(D.unit_mask, nu, c->units, c->d_nunits);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(&c->nunits_active, c->d_nunits, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess)
+            return e;
+    }
     return cudaStreamSynchronize(s);
 }
 
