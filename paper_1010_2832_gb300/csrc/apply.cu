@@ -216,6 +216,268 @@ __global__ void __launch_bounds__(256, MINB) k_apply2d(Layout L, const int* __re
     }
 }
 
+// 2D apply with FP32 vectors, four slots per thread: a CTA of 256 threads
+// is four groups of 64, each working on its own 32 x 8 tile of the list
+// (persistent: group g of CTA b takes tiles 4 b + g, 4 b + g + 4 G, ...)
+// and synchronising on its own named barrier.  Every load of a row's 32
+// slots is one 16-byte load per field for the vectors (8 bytes for BF16
+// coefficients, 16 for FP32), plus scalar loads for the two halo columns:
+// about 5 load instructions per slot against 17 with one slot per thread.
+// Every load of a tile is issued before any is used (one memory round trip
+// per tile; 127 registers, two CTAs = eight tiles in flight per SM): FP32 on
+// a 4096^2 box 0.77 of the measured HBM bandwidth (one slot per thread,
+// software-pipelined: 0.69; this layout with a round trip per phase: 0.63).
+// The arithmetic of each slot is that of apply2d_tile, in the same order.
+// Four consecutive coefficients as loaded (R: float4, or uint2 holding four
+// BF16 values, converted only where used, so that a tile's loads in flight
+// take half the registers) and as FP32.
+template <class C> struct V4;
+template <> struct V4<float> {
+    using R = float4;
+    static __device__ __forceinline__ R ld(const float* p, int64_t o) {
+        return __ldg(reinterpret_cast<const float4*>(p + o));
+    }
+    static __device__ __forceinline__ float4 f(const R& r) { return r; }
+};
+template <> struct V4<__nv_bfloat16> {
+    using R = uint2;
+    static __device__ __forceinline__ R ld(const __nv_bfloat16* p, int64_t o) {
+        return __ldg(reinterpret_cast<const uint2*>(p + o));
+    }
+    static __device__ __forceinline__ float4 f(const R& w) {
+        return make_float4(__uint_as_float(w.x << 16), __uint_as_float(w.x & 0xffff0000u), __uint_as_float(w.y << 16),
+                           __uint_as_float(w.y & 0xffff0000u));
+    }
+};
+__device__ __forceinline__ float f4(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+
+struct Smem2v {
+    float U[TY2 + 2][TX + 2], V[TY2 + 2][TX + 2], N[TY2 + 2][TX + 2];
+    float Zu[TY2 + 1][TX + 1], Zv[TY2 + 1][TX + 1];
+    float own[3][TY2][TX];
+};
+
+template <class C, int MODE>
+__global__ void __launch_bounds__(256, 2) k_apply2d_v4(Layout L, const int* __restrict__ tiles, Coef<C> cf,
+                                                       const float* __restrict__ x, float* __restrict__ y,
+                                                       ApplyArgs args, int ntiles) {
+    __shared__ __align__(16) Smem2v smg[4];
+    if (MODE == MODE_CG && args.sc->done) return;
+    const float beta = MODE == MODE_CG ? (float)args.sc->beta : 0.f;
+    const float* __restrict__ pold = (const float*)args.pold;
+    float* __restrict__ pnew = (float*)args.pnew;
+    const float* __restrict__ b = (const float*)args.b;
+    const int64_t S = L.stride;
+    const int g = threadIdx.x >> 6, l = threadIdx.x & 63;
+    Smem2v& sm = smg[g];
+    const C *a_c = cf.f[0], *a_n = cf.f[1], *d_c = cf.f[2], *d_n = cf.f[3], *K_u = cf.f[4], *K_v = cf.f[5];
+    auto gsync = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(1 + g) : "memory"); };
+    // the thread's items of one tile: a staged quad (row l/8 of rows 0..7),
+    // a second staged quad (rows 8, 9) or a halo-column pair of values, up to
+    // three face quads or leftover faces, and its own output quad
+    constexpr int NFQ = 2 * (TY2 + 1) * 8 + 2 * (TY2 + 1);   // 144 face quads + 18 single faces
+    using CR = typename V4<C>::R;
+    struct Loads {
+        float4 xa[3], pa[3];
+        CR aca, ana;                       // staged quad A
+        float4 xb[3], pb[3];
+        CR acb, anb;                       // staged quad B (l < 16)
+        float hac, han;                    // or halo values (l < 36: .x of xb, pb)
+        CR kf[3];                          // face coefficients (quads)
+        float kf1[3];                      // or single faces
+        CR oac, oan, odc, odn;             // own quad
+        float4 ob[3];
+    };
+    auto load_tile = [&](int c0, int r0, Loads& d) {
+        {
+            const int64_t o = L.off(c0 + 4 * (l & 7), r0 - 1 + (l >> 3), 0);
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                d.xa[f] = __ldg(reinterpret_cast<const float4*>(x + f * S + o));
+                if (MODE == MODE_CG) d.pa[f] = __ldg(reinterpret_cast<const float4*>(pold + f * S + o));
+            }
+            d.aca = V4<C>::ld(a_c, o);
+            d.ana = V4<C>::ld(a_n, o);
+        }
+        if (l < 16) {
+            const int64_t o = L.off(c0 + 4 * (l & 7), r0 + 7 + (l >> 3), 0);
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                d.xb[f] = __ldg(reinterpret_cast<const float4*>(x + f * S + o));
+                if (MODE == MODE_CG) d.pb[f] = __ldg(reinterpret_cast<const float4*>(pold + f * S + o));
+            }
+            d.acb = V4<C>::ld(a_c, o);
+            d.anb = V4<C>::ld(a_n, o);
+        } else if (l < 16 + 2 * (TY2 + 2)) {
+            const int e = l - 16, jj = e >> 1, ii = (e & 1) ? TX + 1 : 0;
+            const int64_t o = L.off(c0 - 1 + ii, r0 - 1 + jj, 0);
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                d.xb[f].x = __ldg(x + f * S + o);
+                if (MODE == MODE_CG) d.pb[f].x = __ldg(pold + f * S + o);
+            }
+            d.hac = ld<float, C>(a_c, o);
+            d.han = ld<float, C>(a_n, o);
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const int it = l + 64 * u;
+            if (it < 2 * (TY2 + 1) * 8) {
+                const int dir = it / ((TY2 + 1) * 8), rem = it - dir * ((TY2 + 1) * 8), jj = rem >> 3, qd = rem & 7;
+                d.kf[u] = dir == 0 ? V4<C>::ld(K_u, L.off(c0 + 4 * qd, r0 - 1 + jj, 0))
+                                   : V4<C>::ld(K_v, L.off(c0 + 4 * qd, r0 + jj, 0));
+            } else if (it < NFQ) {
+                const int e = it - 2 * (TY2 + 1) * 8, jj = e >> 1;
+                d.kf1[u] = (e & 1) ? ld<float, C>(K_u, L.off(c0 + TX, r0 - 1 + jj, 0))
+                                   : ld<float, C>(K_v, L.off(c0 - 1, r0 + jj, 0));
+            }
+        }
+        {
+            const int64_t o = L.off(c0 + 4 * (l & 7), r0 + (l >> 3), 0);
+            d.oac = V4<C>::ld(a_c, o);
+            d.oan = V4<C>::ld(a_n, o);
+            d.odc = V4<C>::ld(d_c, o);
+            d.odn = V4<C>::ld(d_n, o);
+            if (MODE == MODE_RESID) {
+#pragma unroll
+                for (int f = 0; f < 3; ++f) d.ob[f] = __ldg(reinterpret_cast<const float4*>(b + f * S + o));
+            }
+        }
+    };
+    // staged quad at staged row jj, columns ii..ii+3 (ii = 1 + 4 qd)
+    auto stage_quad = [&](int c0, int r0, int jj, int qd, float4 (&vx)[3], const float4 (&po)[3], const CR& acr,
+                          const CR& anr) {
+        const float4 ac = V4<C>::f(acr), an = V4<C>::f(anr);
+        const int ii = 1 + 4 * qd;
+        if (MODE == MODE_CG) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                vx[f].x += beta * po[f].x; vx[f].y += beta * po[f].y;
+                vx[f].z += beta * po[f].z; vx[f].w += beta * po[f].w;
+            }
+        }
+        if (jj >= 1 && jj <= TY2) {
+            if (MODE == MODE_CG) {
+                const int64_t o = L.off(c0 + 4 * qd, r0 - 1 + jj, 0);
+#pragma unroll
+                for (int f = 0; f < 3; ++f) *reinterpret_cast<float4*>(pnew + f * S + o) = vx[f];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                sm.own[0][jj - 1][ii - 1 + i] = f4(vx[0], i);
+                sm.own[1][jj - 1][ii - 1 + i] = f4(vx[1], i);
+                sm.own[2][jj - 1][ii - 1 + i] = f4(vx[2], i);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float txx = f4(vx[0], i), txy = f4(vx[1], i), p = f4(vx[2], i);
+            sm.U[jj][ii + i] = f4(ac, i) * (p - txx);
+            sm.V[jj][ii + i] = f4(ac, i) * (p + txx);
+            sm.N[jj][ii + i] = f4(an, i) * txy;
+        }
+    };
+    Acc<float> acc;
+    for (int k = blockIdx.x * 4 + g; k < ntiles; k += gridDim.x * 4) {
+        const int tile = tiles ? tiles[k] : k;
+        const int c0 = (tile % L.ntx) * TX, r0 = (tile / L.ntx) * TY2;
+        // every global load of the tile is issued first: one memory round trip
+        Loads d;
+        load_tile(c0, r0, d);
+        // 1. stage (p = z + beta p_old in CG mode)
+        stage_quad(c0, r0, l >> 3, l & 7, d.xa, d.pa, d.aca, d.ana);
+        if (l < 16) {
+            stage_quad(c0, r0, 8 + (l >> 3), l & 7, d.xb, d.pb, d.acb, d.anb);
+        } else if (l < 16 + 2 * (TY2 + 2)) {
+            const int e = l - 16, jj = e >> 1, ii = (e & 1) ? TX + 1 : 0;
+            float v[3];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) v[f] = MODE == MODE_CG ? d.xb[f].x + beta * d.pb[f].x : d.xb[f].x;
+            sm.U[jj][ii] = d.hac * (v[2] - v[0]);
+            sm.V[jj][ii] = d.hac * (v[2] + v[0]);
+            sm.N[jj][ii] = d.han * v[1];
+        }
+        gsync();
+        // 2. faces z_u (ii = 0..32 at columns c0 + ii) and z_v (ii = 0..32 at
+        // columns c0 - 1 + ii), rows jj = 0..8: quads of four, and the one
+        // face left over in each row (z_u: ii = 32; z_v: ii = 0)
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const int it = l + 64 * u;
+            if (it < 2 * (TY2 + 1) * 8) {
+                const int dir = it / ((TY2 + 1) * 8), rem = it - dir * ((TY2 + 1) * 8), jj = rem >> 3, qd = rem & 7;
+                const float4 k4 = V4<C>::f(d.kf[u]);
+                if (dir == 0) {
+                    const int ii = 4 * qd;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        sm.Zu[jj][ii + i] = f4(k4, i) * ((sm.U[jj][ii + i + 1] - sm.U[jj][ii + i]) +
+                                                         (sm.N[jj][ii + i + 1] - sm.N[jj + 1][ii + i + 1]));
+                } else {
+                    const int ii = 1 + 4 * qd;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        sm.Zv[jj][ii + i] = f4(k4, i) * ((sm.V[jj + 1][ii + i] - sm.V[jj][ii + i]) +
+                                                         (sm.N[jj + 1][ii + i] - sm.N[jj + 1][ii + i + 1]));
+                }
+            } else if (it < NFQ) {
+                const int e = it - 2 * (TY2 + 1) * 8, jj = e >> 1;
+                if (e & 1)
+                    sm.Zu[jj][TX] = d.kf1[u] * ((sm.U[jj][TX + 1] - sm.U[jj][TX]) +
+                                                (sm.N[jj][TX + 1] - sm.N[jj + 1][TX + 1]));
+                else
+                    sm.Zv[jj][0] = d.kf1[u] * ((sm.V[jj + 1][0] - sm.V[jj][0]) + (sm.N[jj + 1][0] - sm.N[jj + 1][1]));
+            }
+        }
+        gsync();
+        // 3. y = C x + B z on the thread's own quad (row ty, columns 4 qd..4 qd+3)
+        {
+            const int ty = l >> 3, qd = l & 7;
+            const int64_t o = L.off(c0 + 4 * qd, r0 + ty, 0);
+            float yo[3][4];
+            const float4 oac = V4<C>::f(d.oac), oan = V4<C>::f(d.oan), odc = V4<C>::f(d.odc), odn = V4<C>::f(d.odn);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int tx = 4 * qd + i;
+                const float ac = f4(oac, i), an = f4(oan, i), dc = f4(odc, i), dn = f4(odn, i);
+                const float txx = sm.own[0][ty][tx], txy = sm.own[1][ty][tx], p_ = sm.own[2][ty][tx];
+                const float zu = sm.Zu[ty + 1][tx], zur = sm.Zu[ty + 1][tx + 1], zud = sm.Zu[ty][tx];
+                const float zv = sm.Zv[ty][tx + 1], zvu = sm.Zv[ty + 1][tx + 1], zvl = sm.Zv[ty][tx];
+                float yp, yxx;
+                if (ac != 0.f) {
+                    yp = ac * ((zu - zur) + (zv - zvu));
+                    yxx = dc * txx + ac * ((zur - zu) + (zv - zvu));
+                } else {
+                    yp = p_;
+                    yxx = txx;
+                }
+                float yxy = dn * txy + an * ((zu - zud) + (zv - zvl));
+                if (MODE == MODE_RESID) {
+                    yxx = f4(d.ob[0], i) - yxx; yxy = f4(d.ob[1], i) - yxy; yp = f4(d.ob[2], i) - yp;
+                }
+                yo[0][i] = yxx; yo[1][i] = yxy; yo[2][i] = yp;
+                if (MODE == MODE_RESID) { acc.add(yxx, yxx); acc.add(yxy, yxy); acc.add(yp, yp); }
+                else if (MODE == MODE_CG) { acc.add(txx, yxx); acc.add(txy, yxy); acc.add(p_, yp); }
+            }
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+                *reinterpret_cast<float4*>(y + f * S + o) = make_float4(yo[f][0], yo[f][1], yo[f][2], yo[f][3]);
+        }
+        gsync();                                 // the next tile's staging reuses the group's shared memory
+    }
+    if (MODE != MODE_PLAIN) {
+        double v = acc.warp();
+        if ((threadIdx.x & 31) != 0) v = 0.0;
+        CgScalars* sc = args.sc;
+        block_partial_and_finish<256>(v, args.partial, args.counter, gridDim.x, [&](double tot) {
+            if (MODE == MODE_RESID) { sc->rr = tot; return; }
+            sc->pq = tot;
+            if (!(tot > 0.0) || !isfinite(tot)) { sc->done = 1; sc->status = (isfinite(tot) ? STOKES_ERR_BREAKDOWN : STOKES_ERR_NONFINITE); }
+            else sc->alpha = sc->rz / tot;
+        });
+    }
+}
+
 // ------------------------------- 3D -----------------------------------------
 // Staged helpers per slot (tile + halo):
 //   Uc = a_c (p - txx), Vc = a_c (p - tyy), Wc = a_c (p + txx + tyy)
@@ -485,14 +747,17 @@ static cudaError_t launch_mode(const Layout& L, const int* tiles, int ntiles, co
     if (ntiles <= 0) return cudaSuccess;
     static int cache2[16], cache3[16];
     if (L.dim == 2) {
-        // FP32 vectors: at most 64 registers, four CTAs per SM (measured 70% of
-        // HBM at 4096^2, against 54% with 96 registers and three CTAs, 67% with
-        // five); BF16 coefficients: five CTAs per SM (44% against 38% with
-        // four); FP64 is bound by the FP64 pipe, where the unconstrained build
-        // is faster
-        constexpr int MINB = sizeof(C) == 2 ? 5 : (sizeof(T) == 4 ? 4 : 1);
-        const int grid = std::min(ntiles, resident_ctas((const void*)k_apply2d<T, C, MODE, MINB>, 256, 0, cache2));
-        k_apply2d<T, C, MODE, MINB><<<grid, 256, 0, s>>>(L, tiles, cf, x, y, a, ntiles);
+        // FP64 vectors: one slot per thread, software-pipelined over the tiles
+        // (bound by the FP64 pipe; the unconstrained build is faster)
+        if constexpr (sizeof(T) == 4) {
+            // FP32 vectors: four slots per thread, four tiles per CTA
+            const int grid = std::min((ntiles + 3) / 4, resident_ctas((const void*)k_apply2d_v4<C, MODE>, 256, 0, cache2));
+            k_apply2d_v4<C, MODE><<<grid, 256, 0, s>>>(L, tiles, cf, x, y, a, ntiles);
+        } else {
+            constexpr int MINB = 1;
+            const int grid = std::min(ntiles, resident_ctas((const void*)k_apply2d<T, C, MODE, MINB>, 256, 0, cache2));
+            k_apply2d<T, C, MODE, MINB><<<grid, 256, 0, s>>>(L, tiles, cf, x, y, a, ntiles);
+        }
     } else {
         // 3D: one CTA per unit (32 x 8 slots, 16 planes), over the active
         // units (an apply over the active tiles needs the unit list) or all
