@@ -42,7 +42,7 @@ KERNEL_SOURCES = {
 # (workload, mode, kernel) -> (source hash, dram__bytes_read.sum +
 # dram__bytes_write.sum per launch from one ncu capture of the same command)
 NCU_TRAFFIC = {
-    ("bumps1024", "fp32", "k_schwarz_gemv"): ("92fa288fa39359d4", 245.15456e6),   # ncu capture of this command
+    ("bumps1024", "fp32", "k_schwarz_gemv"): ("5b8e7f14a3700538", 244.706048e6),   # ncu capture of this command
 }
 
 
@@ -899,7 +899,14 @@ def main():
     ap.add_argument("--quick", action="store_true", help="timed steps only (for profiler runs)")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven CG loop (profilers cannot enter conditional graphs)")
+    ap.add_argument("--dense-apply-only", metavar="DIM:N:PREC",
+                    help="only the CG-mode apply on an N^DIM box full of liquid (PREC 0 FP64, 1 FP32, 2 BF16 "
+                         "coefficients): one JSON line (for profiler runs)")
     args = ap.parse_args()
+    if args.dense_apply_only:
+        dim, n, prec = (int(v) for v in args.dense_apply_only.split(":"))
+        print(json.dumps(dense_apply(dim, n, prec, hbm_peak()[0])))
+        return
     if args.quick:
         args.no_cpu_baseline = True
         args.no_dense_apply = True
