@@ -749,10 +749,23 @@ static cudaError_t launch_mode(const Layout& L, const int* tiles, int ntiles, co
     if (L.dim == 2) {
         // FP64 vectors: one slot per thread, software-pipelined over the tiles
         // (bound by the FP64 pipe; the unconstrained build is faster)
+        // FP32 vectors: four slots per thread, four tiles per CTA, 16-byte
+        // loads and stores of the vectors, which callers' arrays (a view at
+        // an odd offset) need not allow: those take one slot per thread
+        const bool aligned = (((uintptr_t)x | (uintptr_t)y | (uintptr_t)a.pold | (uintptr_t)a.pnew |
+                               (uintptr_t)a.b) & 15u) == 0;
         if constexpr (sizeof(T) == 4) {
-            // FP32 vectors: four slots per thread, four tiles per CTA
-            const int grid = std::min((ntiles + 3) / 4, resident_ctas((const void*)k_apply2d_v4<C, MODE>, 256, 0, cache2));
-            k_apply2d_v4<C, MODE><<<grid, 256, 0, s>>>(L, tiles, cf, x, y, a, ntiles);
+            if (aligned) {
+                const int grid =
+                    std::min((ntiles + 3) / 4, resident_ctas((const void*)k_apply2d_v4<C, MODE>, 256, 0, cache2));
+                k_apply2d_v4<C, MODE><<<grid, 256, 0, s>>>(L, tiles, cf, x, y, a, ntiles);
+            } else {
+                static int cache1[16];
+                constexpr int MINB = sizeof(C) == 2 ? 5 : 4;
+                const int grid =
+                    std::min(ntiles, resident_ctas((const void*)k_apply2d<T, C, MODE, MINB>, 256, 0, cache1));
+                k_apply2d<T, C, MODE, MINB><<<grid, 256, 0, s>>>(L, tiles, cf, x, y, a, ntiles);
+            }
         } else {
             constexpr int MINB = 1;
             const int grid = std::min(ntiles, resident_ctas((const void*)k_apply2d<T, C, MODE, MINB>, 256, 0, cache2));

@@ -101,6 +101,36 @@ def test_apply_matches_oracle(name, prec, tol):
     assert np.all(err <= tol * scale + 1e-300), (err / np.maximum(scale, 1e-300)).max()
 
 
+@pytest.mark.parametrize("name", ["rand2d_a", "bumps96"])
+@pytest.mark.parametrize("prec", [1, 2])
+def test_apply_fp32_vectors_at_any_alignment(name, prec):
+    """The FP32 apply moves 16 bytes per load where the vectors start on a
+    16-byte boundary; vectors 4, 8 or 12 bytes past one take the
+    one-slot-per-thread kernel.  Both match the oracle and each other (to
+    FP32 rounding: the two kernels may contract the same expressions into
+    FMAs differently)."""
+    from paper_1010_2832_gb300 import stokes
+    wl, S, ctx, dev = setup(name)
+    rng = np.random.default_rng(7 + prec)
+    x = rng.uniform(-1, 1, S.A.shape[0])
+    scale = abs_matvec(S.A, x)
+    x32 = ctx.fields_to_slots(to_gpu(x)).to(torch.float32)
+    y_al = ctx.new_vector(torch.float32)
+    ctx.apply(x32, y_al, prec)
+    n = x32.numel()
+    for off in (1, 2, 3):
+        xb = torch.zeros(n + 4, dtype=torch.float32, device="cuda")
+        yb = torch.full((n + 4,), float("nan"), dtype=torch.float32, device="cuda")
+        xv, yv = xb[off:off + n], yb[off:off + n]
+        xv.copy_(x32)
+        assert xv.data_ptr() % 16 != 0 and yv.data_ptr() % 16 != 0
+        ctx.apply(xv, yv, prec)
+        y = ctx.slots_to_fields(yv.to(torch.float64)).cpu().numpy()
+        y_ref = ctx.slots_to_fields(y_al.to(torch.float64)).cpu().numpy()
+        assert np.all(np.abs(y - y_ref) <= 1e-6 * scale + 1e-300)
+        assert np.all(np.abs(y - S.A @ x) <= (1e-5 if prec == 1 else 2e-2) * scale + 1e-300)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_rhs_and_recovery_match(name):
     wl, S, ctx, dev = setup(name)
