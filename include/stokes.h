@@ -151,7 +151,9 @@ stokes_status stokes_vector_layout(stokes_ctx ctx, stokes_layout* out);
  * Section 7: face values z = K B^T x, then y = B z + C x).  x, y are device
  * vectors in slot layout of element type double (STOKES_FP64) or float
  * (STOKES_FP32, STOKES_BF16).  Inactive unknowns act as the identity.
- * Requires stokes_build_weights.  x and y must not alias.
+ * Requires stokes_build_weights.  x and y must not alias.  Any element
+ * alignment is accepted; in 2D, float vectors that both start on a 16-byte
+ * boundary are read and written 16 bytes at a time (the faster kernel).
  */
 stokes_status stokes_apply(stokes_ctx ctx, const void* x, void* y, int precision);
 
