@@ -271,7 +271,9 @@ stokes_status stokes_advect(stokes_ctx ctx, const double* const* u_in, const dou
  * p_out are device arrays in field layout; inactive unknowns come out 0.
  * Synchronises the context's stream once at the end to fill ``stats``
  * (may be NULL).  Returns STOKES_ERR_NOT_CONVERGED with the best x found if
- * the caps are reached first.
+ * the caps are reached first.  A grid with no active unknown (no liquid)
+ * has an empty system: the call returns STOKES_OK after 0 iterations with
+ * x = 0 (u = u_BC on solid faces, u* elsewhere).
  */
 stokes_status stokes_solve_step(stokes_ctx ctx, const double* const* u_star, double* const* u_out,
                                 double* const* tau_out, double* p_out, const stokes_options* opt,
