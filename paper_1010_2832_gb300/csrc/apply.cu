@@ -250,6 +250,12 @@ template <> struct V4<__nv_bfloat16> {
     }
 };
 __device__ __forceinline__ float f4(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+// a pair word of the BF16 pair arrays: first coefficient (low half), second
+__device__ __forceinline__ float plo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float phi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+__device__ __forceinline__ float4 plo4(const uint4& q) { return make_float4(plo(q.x), plo(q.y), plo(q.z), plo(q.w)); }
+__device__ __forceinline__ float4 phi4(const uint4& q) { return make_float4(phi(q.x), phi(q.y), phi(q.z), phi(q.w)); }
+__device__ __forceinline__ uint32_t u4(const uint4& q, int i) { return i == 0 ? q.x : i == 1 ? q.y : i == 2 ? q.z : q.w; }
 
 struct Smem2v {
     float U[TY2 + 2][TX + 2], V[TY2 + 2][TX + 2], N[TY2 + 2][TX + 2];
@@ -277,6 +283,16 @@ __global__ void __launch_bounds__(256, 2) k_apply2d_v4(Layout L, const int* __re
     // three face quads or leftover faces, and its own output quad
     constexpr int NFQ = 2 * (TY2 + 1) * 8 + 2 * (TY2 + 1);   // 144 face quads + 18 single faces
     using CR = typename V4<C>::R;
+    // BF16 coefficients come from the pair arrays: the staged and own quads'
+    // (a_c, a_n) and (d_c, d_n) in one 16-byte load each, and the faces as
+    // (K_u, K_v) quads of the ten rows r0-1 .. r0+8 (row r0-1+jr gives the
+    // u faces of row jr and the v faces of row jr-1): 80 face loads a tile
+    // instead of 144
+    constexpr bool PAIR = sizeof(C) == 2;
+    constexpr int NKQ = (TY2 + 2) * 8;                       // 80 pair quads
+    const uint32_t* __restrict__ pac = cf.pr[0];
+    const uint32_t* __restrict__ pdc = cf.pr[1];
+    const uint32_t* __restrict__ pku = cf.pr[2];
     struct Loads {
         float4 xa[3], pa[3];
         CR aca, ana;                       // staged quad A
@@ -287,6 +303,8 @@ __global__ void __launch_bounds__(256, 2) k_apply2d_v4(Layout L, const int* __re
         float kf1[3];                      // or single faces
         CR oac, oan, odc, odn;             // own quad
         float4 ob[3];
+        uint4 ppa, ppb, kq[2], opa, opd;   // pair form (BF16)
+        uint32_t hp, ks;
     };
     auto load_tile = [&](int c0, int r0, Loads& d) {
         {
@@ -296,8 +314,12 @@ __global__ void __launch_bounds__(256, 2) k_apply2d_v4(Layout L, const int* __re
                 d.xa[f] = __ldg(reinterpret_cast<const float4*>(x + f * S + o));
                 if (MODE == MODE_CG) d.pa[f] = __ldg(reinterpret_cast<const float4*>(pold + f * S + o));
             }
-            d.aca = V4<C>::ld(a_c, o);
-            d.ana = V4<C>::ld(a_n, o);
+            if constexpr (PAIR) {
+                d.ppa = __ldg(reinterpret_cast<const uint4*>(pac + o));
+            } else {
+                d.aca = V4<C>::ld(a_c, o);
+                d.ana = V4<C>::ld(a_n, o);
+            }
         }
         if (l < 16) {
             const int64_t o = L.off(c0 + 4 * (l & 7), r0 + 7 + (l >> 3), 0);
@@ -306,8 +328,12 @@ __global__ void __launch_bounds__(256, 2) k_apply2d_v4(Layout L, const int* __re
                 d.xb[f] = __ldg(reinterpret_cast<const float4*>(x + f * S + o));
                 if (MODE == MODE_CG) d.pb[f] = __ldg(reinterpret_cast<const float4*>(pold + f * S + o));
             }
-            d.acb = V4<C>::ld(a_c, o);
-            d.anb = V4<C>::ld(a_n, o);
+            if constexpr (PAIR) {
+                d.ppb = __ldg(reinterpret_cast<const uint4*>(pac + o));
+            } else {
+                d.acb = V4<C>::ld(a_c, o);
+                d.anb = V4<C>::ld(a_n, o);
+            }
         } else if (l < 16 + 2 * (TY2 + 2)) {
             const int e = l - 16, jj = e >> 1, ii = (e & 1) ? TX + 1 : 0;
             const int64_t o = L.off(c0 - 1 + ii, r0 - 1 + jj, 0);
@@ -316,9 +342,25 @@ __global__ void __launch_bounds__(256, 2) k_apply2d_v4(Layout L, const int* __re
                 d.xb[f].x = __ldg(x + f * S + o);
                 if (MODE == MODE_CG) d.pb[f].x = __ldg(pold + f * S + o);
             }
-            d.hac = ld<float, C>(a_c, o);
-            d.han = ld<float, C>(a_n, o);
+            if constexpr (PAIR) {
+                d.hp = __ldg(pac + o);
+            } else {
+                d.hac = ld<float, C>(a_c, o);
+                d.han = ld<float, C>(a_n, o);
+            }
         }
+        if constexpr (PAIR) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int it = l + 64 * u;
+                if (it < NKQ) {
+                    d.kq[u] = __ldg(reinterpret_cast<const uint4*>(pku + L.off(c0 + 4 * (it & 7), r0 - 1 + (it >> 3), 0)));
+                } else if (it < NKQ + 2 * (TY2 + 1)) {
+                    const int e = it - NKQ, jj = e >> 1;
+                    d.ks = (e & 1) ? __ldg(pku + L.off(c0 + TX, r0 - 1 + jj, 0)) : __ldg(pku + L.off(c0 - 1, r0 + jj, 0));
+                }
+            }
+        } else {
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
             const int it = l + 64 * u;
@@ -332,12 +374,18 @@ __global__ void __launch_bounds__(256, 2) k_apply2d_v4(Layout L, const int* __re
                                    : ld<float, C>(K_v, L.off(c0 - 1, r0 + jj, 0));
             }
         }
+        }
         {
             const int64_t o = L.off(c0 + 4 * (l & 7), r0 + (l >> 3), 0);
-            d.oac = V4<C>::ld(a_c, o);
-            d.oan = V4<C>::ld(a_n, o);
-            d.odc = V4<C>::ld(d_c, o);
-            d.odn = V4<C>::ld(d_n, o);
+            if constexpr (PAIR) {
+                d.opa = __ldg(reinterpret_cast<const uint4*>(pac + o));
+                d.opd = __ldg(reinterpret_cast<const uint4*>(pdc + o));
+            } else {
+                d.oac = V4<C>::ld(a_c, o);
+                d.oan = V4<C>::ld(a_n, o);
+                d.odc = V4<C>::ld(d_c, o);
+                d.odn = V4<C>::ld(d_n, o);
+            }
             if (MODE == MODE_RESID) {
 #pragma unroll
                 for (int f = 0; f < 3; ++f) d.ob[f] = __ldg(reinterpret_cast<const float4*>(b + f * S + o));
@@ -345,9 +393,8 @@ __global__ void __launch_bounds__(256, 2) k_apply2d_v4(Layout L, const int* __re
         }
     };
     // staged quad at staged row jj, columns ii..ii+3 (ii = 1 + 4 qd)
-    auto stage_quad = [&](int c0, int r0, int jj, int qd, float4 (&vx)[3], const float4 (&po)[3], const CR& acr,
-                          const CR& anr) {
-        const float4 ac = V4<C>::f(acr), an = V4<C>::f(anr);
+    auto stage_quad = [&](int c0, int r0, int jj, int qd, float4 (&vx)[3], const float4 (&po)[3], const float4 ac,
+                          const float4 an) {
         const int ii = 1 + 4 * qd;
         if (MODE == MODE_CG) {
 #pragma unroll
@@ -385,22 +432,55 @@ __global__ void __launch_bounds__(256, 2) k_apply2d_v4(Layout L, const int* __re
         Loads d;
         load_tile(c0, r0, d);
         // 1. stage (p = z + beta p_old in CG mode)
-        stage_quad(c0, r0, l >> 3, l & 7, d.xa, d.pa, d.aca, d.ana);
+        if constexpr (PAIR) stage_quad(c0, r0, l >> 3, l & 7, d.xa, d.pa, plo4(d.ppa), phi4(d.ppa));
+        else stage_quad(c0, r0, l >> 3, l & 7, d.xa, d.pa, V4<C>::f(d.aca), V4<C>::f(d.ana));
         if (l < 16) {
-            stage_quad(c0, r0, 8 + (l >> 3), l & 7, d.xb, d.pb, d.acb, d.anb);
+            if constexpr (PAIR) stage_quad(c0, r0, 8 + (l >> 3), l & 7, d.xb, d.pb, plo4(d.ppb), phi4(d.ppb));
+            else stage_quad(c0, r0, 8 + (l >> 3), l & 7, d.xb, d.pb, V4<C>::f(d.acb), V4<C>::f(d.anb));
         } else if (l < 16 + 2 * (TY2 + 2)) {
             const int e = l - 16, jj = e >> 1, ii = (e & 1) ? TX + 1 : 0;
             float v[3];
 #pragma unroll
             for (int f = 0; f < 3; ++f) v[f] = MODE == MODE_CG ? d.xb[f].x + beta * d.pb[f].x : d.xb[f].x;
-            sm.U[jj][ii] = d.hac * (v[2] - v[0]);
-            sm.V[jj][ii] = d.hac * (v[2] + v[0]);
-            sm.N[jj][ii] = d.han * v[1];
+            const float hac = PAIR ? plo(d.hp) : d.hac, han = PAIR ? phi(d.hp) : d.han;
+            sm.U[jj][ii] = hac * (v[2] - v[0]);
+            sm.V[jj][ii] = hac * (v[2] + v[0]);
+            sm.N[jj][ii] = han * v[1];
         }
         gsync();
         // 2. faces z_u (ii = 0..32 at columns c0 + ii) and z_v (ii = 0..32 at
         // columns c0 - 1 + ii), rows jj = 0..8: quads of four, and the one
         // face left over in each row (z_u: ii = 32; z_v: ii = 0)
+        if constexpr (PAIR) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int it = l + 64 * u;
+                if (it < NKQ) {
+                    const int jr = it >> 3, qd = it & 7;
+                    if (jr <= TY2) {
+                        const int jj = jr, ii = 4 * qd;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            sm.Zu[jj][ii + i] = plo(u4(d.kq[u], i)) * ((sm.U[jj][ii + i + 1] - sm.U[jj][ii + i]) +
+                                                                       (sm.N[jj][ii + i + 1] - sm.N[jj + 1][ii + i + 1]));
+                    }
+                    if (jr >= 1) {
+                        const int jj = jr - 1, ii = 1 + 4 * qd;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            sm.Zv[jj][ii + i] = phi(u4(d.kq[u], i)) * ((sm.V[jj + 1][ii + i] - sm.V[jj][ii + i]) +
+                                                                       (sm.N[jj + 1][ii + i] - sm.N[jj + 1][ii + i + 1]));
+                    }
+                } else if (it < NKQ + 2 * (TY2 + 1)) {
+                    const int e = it - NKQ, jj = e >> 1;
+                    if (e & 1)
+                        sm.Zu[jj][TX] = plo(d.ks) * ((sm.U[jj][TX + 1] - sm.U[jj][TX]) +
+                                                     (sm.N[jj][TX + 1] - sm.N[jj + 1][TX + 1]));
+                    else
+                        sm.Zv[jj][0] = phi(d.ks) * ((sm.V[jj + 1][0] - sm.V[jj][0]) + (sm.N[jj + 1][0] - sm.N[jj + 1][1]));
+                }
+            }
+        } else {
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
             const int it = l + 64 * u;
@@ -429,13 +509,15 @@ __global__ void __launch_bounds__(256, 2) k_apply2d_v4(Layout L, const int* __re
                     sm.Zv[jj][0] = d.kf1[u] * ((sm.V[jj + 1][0] - sm.V[jj][0]) + (sm.N[jj + 1][0] - sm.N[jj + 1][1]));
             }
         }
+        }
         gsync();
         // 3. y = C x + B z on the thread's own quad (row ty, columns 4 qd..4 qd+3)
         {
             const int ty = l >> 3, qd = l & 7;
             const int64_t o = L.off(c0 + 4 * qd, r0 + ty, 0);
             float yo[3][4];
-            const float4 oac = V4<C>::f(d.oac), oan = V4<C>::f(d.oan), odc = V4<C>::f(d.odc), odn = V4<C>::f(d.odn);
+            const float4 oac = PAIR ? plo4(d.opa) : V4<C>::f(d.oac), oan = PAIR ? phi4(d.opa) : V4<C>::f(d.oan);
+            const float4 odc = PAIR ? plo4(d.opd) : V4<C>::f(d.odc), odn = PAIR ? phi4(d.opd) : V4<C>::f(d.odn);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int tx = 4 * qd + i;
@@ -755,7 +837,7 @@ static cudaError_t launch_mode(const Layout& L, const int* tiles, int ntiles, co
         const bool aligned = (((uintptr_t)x | (uintptr_t)y | (uintptr_t)a.pold | (uintptr_t)a.pnew |
                                (uintptr_t)a.b) & 15u) == 0;
         if constexpr (sizeof(T) == 4) {
-            if (aligned) {
+            if (aligned && (sizeof(C) == 4 || cf.pr[0])) {
                 const int grid =
                     std::min((ntiles + 3) / 4, resident_ctas((const void*)k_apply2d_v4<C, MODE>, 256, 0, cache2));
                 k_apply2d_v4<C, MODE><<<grid, 256, 0, s>>>(L, tiles, cf, x, y, a, ntiles);

@@ -22,6 +22,7 @@ struct DevArrays {
     double* coef64;
     float* coef32;
     __nv_bfloat16* coef16;
+    uint32_t* pair16;     // 2D: coef16 in pairs (see Coef)
     double* minv64;
     float* minv32;
     uint8_t* tile_flag;
@@ -126,6 +127,8 @@ template <> inline Coef<float> Ctx::coef<float>() const {
 template <> inline Coef<__nv_bfloat16> Ctx::coef<__nv_bfloat16>() const {
     Coef<__nv_bfloat16> c{};
     for (int f = 0; f < ncoef; ++f) c.f[f] = A.coef16 + (int64_t)f * L.stride;
+    if (L.dim == 2 && A.pair16)
+        for (int k = 0; k < 3; ++k) c.pr[k] = A.pair16 + (int64_t)k * L.stride;
     return c;
 }
 

@@ -42,8 +42,13 @@ enum : uint8_t { F_LIVE = 1, F_BAD = 2, F_INVALID = 4, F_WALL = 8, F_EXISTS = 16
 // 3D fields: a_c, a_xy, a_xz, a_yz, d_c, d_xy, d_xz, d_yz, K_u, K_v, K_w.
 // a = W_L / h on active unknowns (0 otherwise); d = W_L W_F / mu on active
 // stress unknowns, 1 on inactive ones; K = dt W_F / (rho W_L) on live faces.
+// 2D BF16 coefficients are also stored in pairs, one 32-bit word per slot
+// (first coefficient in the low half): (a_c, a_n), (d_c, d_n), (K_u, K_v),
+// so that one 16-byte load brings two coefficients of four slots (nullptr
+// in other precisions and in 3D).
 template <class C> struct Coef {
     const C* f[11];
+    const uint32_t* pr[3];
 };
 
 // Device-resident scalars of one CG solve.

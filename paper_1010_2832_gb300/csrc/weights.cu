@@ -539,11 +539,16 @@ __global__ void k_finish2d(Layout L, DevArrays D) {
     // K fields live in the coefficient array as fields 4 and 5
     D.coef64[4 * L.stride + o] = Ku[o];
     D.coef64[5 * L.stride + o] = Kv[o];
+    uint32_t h[6];
     for (int f = 0; f < 6; ++f) {
         double v = D.coef64[(int64_t)f * L.stride + o];
         D.coef32[(int64_t)f * L.stride + o] = (float)v;
-        D.coef16[(int64_t)f * L.stride + o] = __double2bfloat16(v);
+        const __nv_bfloat16 b = __double2bfloat16(v);
+        D.coef16[(int64_t)f * L.stride + o] = b;
+        h[f] = __bfloat16_as_ushort(b);
     }
+    // the same BF16 values in pairs (a_c, a_n), (d_c, d_n), (K_u, K_v)
+    for (int k = 0; k < 3; ++k) D.pair16[(int64_t)k * L.stride + o] = h[2 * k] | (h[2 * k + 1] << 16);
     for (int f = 0; f < 3; ++f) D.minv32[(int64_t)f * L.stride + o] = (float)D.minv64[(int64_t)f * L.stride + o];
     if (tile_act) {
         int c = i + 1, r = j + 1;
