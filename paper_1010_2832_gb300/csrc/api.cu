@@ -185,6 +185,7 @@ stokes_status stokes_create(stokes_ctx* out, const stokes_grid* g, void* stream)
     size_t oC64 = add(sizeof(double) * S * c.ncoef), oC32 = add(sizeof(float) * S * c.ncoef);
     size_t oC16 = add(sizeof(__nv_bfloat16) * S * c.ncoef);
     size_t oP16 = add(g->dim == 2 ? sizeof(uint32_t) * S * 3 : 4);
+    size_t oQ16 = add(g->dim == 3 ? sizeof(uint2) * S * 2 : 8);
     size_t oM64 = add(sizeof(double) * S * c.nf), oM32 = add(sizeof(float) * S * c.nf);
     size_t oTF = add(c.ntiles_all);
     size_t oTF4 = add(g->dim == 2 ? (size_t)L.ntx * (L.R / 4) : 1);
@@ -211,6 +212,7 @@ stokes_status stokes_create(stokes_ctx* out, const stokes_grid* g, void* stream)
         A.coef32 = (float*)(base + oC32);
         A.coef16 = (__nv_bfloat16*)(base + oC16);
         A.pair16 = g->dim == 2 ? (uint32_t*)(base + oP16) : nullptr;
+        A.quad16 = g->dim == 3 ? (uint2*)(base + oQ16) : nullptr;
         A.minv64 = (double*)(base + oM64);
         A.minv32 = (float*)(base + oM32);
         A.tile_flag = (uint8_t*)(base + oTF);

@@ -630,6 +630,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) k_apply3d(Layout 
     const C *a_c = cf.f[0], *a_xy = cf.f[1], *a_xz = cf.f[2], *a_yz = cf.f[3];
     const C *d_c = cf.f[4], *d_xy = cf.f[5], *d_xz = cf.f[6], *d_yz = cf.f[7];
     const C *K_u = cf.f[8], *K_v = cf.f[9], *K_w = cf.f[10];
+    // BF16: a slot's row weights and its diagonal from the arrays in fours
+    // (one 8-byte load each), the face coefficients through L2 only (a warp's
+    // 2-byte loads cover half of a 128-byte line)
+    constexpr bool QD = sizeof(C) == 2;
+    const uint2* __restrict__ qa = cf.qd[0];
+    const uint2* __restrict__ qdg = cf.qd[1];
+    auto ldk = [&](const C* p, int64_t o) -> T {
+        if constexpr (QD) return T(__uint_as_float((uint32_t)__ldcg(reinterpret_cast<const unsigned short*>(p + o)) << 16));
+        else return ld<T, C>(p, o);
+    };
     const T* pold = (const T*)args.pold;
     T* pnew = (T*)args.pnew;
     const T beta = MODE == MODE_CG ? (T)args.sc->beta : T(0);
@@ -661,13 +671,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) k_apply3d(Layout 
 #pragma unroll
                 for (int f = 0; f < 6; ++f) pnew[f * S + o] = v[f];
             }
-            const T ac = ld<T, C>(a_c, o);
+            T ac, axy, axz, ayz;
+            if constexpr (QD) {
+                const uint2 w = __ldg(qa + o);
+                ac = T(plo(w.x)); axy = T(phi(w.x)); axz = T(plo(w.y)); ayz = T(phi(w.y));
+            } else {
+                ac = ld<T, C>(a_c, o); axy = ld<T, C>(a_xy, o); axz = ld<T, C>(a_xz, o); ayz = ld<T, C>(a_yz, o);
+            }
             st[0][e] = ac * (v[5] - v[0]);
             st[1][e] = ac * (v[5] - v[1]);
             st[2][e] = ac * (v[5] + v[0] + v[1]);
-            st[3][e] = ld<T, C>(a_xy, o) * v[2];
-            st[4][e] = ld<T, C>(a_xz, o) * v[3];
-            st[5][e] = ld<T, C>(a_yz, o) * v[4];
+            st[3][e] = axy * v[2];
+            st[4][e] = axz * v[3];
+            st[5][e] = ayz * v[4];
         }
     };
     // face coefficients of z_u(q), z_v(q), z_w(q+1) at face position e (zero
@@ -681,9 +697,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) k_apply3d(Layout 
             if (e < SM::NF) {
                 const int ii = e % SM::FX, jj = e / SM::FX;
                 if (r0 + jj <= L.R) {
-                    k[it][0] = ld<T, C>(K_u, L.off(c0 + ii, r0 - 1 + jj, q));
-                    k[it][1] = ld<T, C>(K_v, L.off(c0 - 1 + ii, r0 + jj, q));
-                    k[it][2] = ld<T, C>(K_w, L.off(c0 - 1 + ii, r0 - 1 + jj, q + 1));
+                    k[it][0] = ldk(K_u, L.off(c0 + ii, r0 - 1 + jj, q));
+                    k[it][1] = ldk(K_v, L.off(c0 - 1 + ii, r0 + jj, q));
+                    k[it][2] = ldk(K_w, L.off(c0 - 1 + ii, r0 - 1 + jj, q + 1));
                 }
             }
         }
@@ -762,7 +778,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) k_apply3d(Layout 
             const T zv_cm = zv_q[fi(tx, ty)], zv_qm = zv_m[fi(tx + 1, ty)];
             const T zw = zw_q[fi(tx + 1, ty + 1)], zw_qp = zw_p[fi(tx + 1, ty + 1)];
             const T zw_cm = zw_q[fi(tx, ty + 1)], zw_rm = zw_q[fi(tx + 1, ty)];
-            const T ac = ld<T, C>(a_c, o), dc = ld<T, C>(d_c, o);
+            T ac, axy, axz, ayz, dc, dxy, dxz, dyz;
+            if constexpr (QD) {
+                const uint2 wa = __ldg(qa + o), wd = __ldg(qdg + o);
+                ac = T(plo(wa.x)); axy = T(phi(wa.x)); axz = T(plo(wa.y)); ayz = T(phi(wa.y));
+                dc = T(plo(wd.x)); dxy = T(phi(wd.x)); dxz = T(plo(wd.y)); dyz = T(phi(wd.y));
+            } else {
+                ac = ld<T, C>(a_c, o); axy = ld<T, C>(a_xy, o); axz = ld<T, C>(a_xz, o); ayz = ld<T, C>(a_yz, o);
+                dc = ld<T, C>(d_c, o); dxy = ld<T, C>(d_xy, o); dxz = ld<T, C>(d_xz, o); dyz = ld<T, C>(d_yz, o);
+            }
             T yv[6];
             if (ac != T(0)) {
                 const T ww = zw - zw_qp;
@@ -772,9 +796,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) k_apply3d(Layout 
             } else {
                 yv[5] = v[5]; yv[0] = v[0]; yv[1] = v[1];
             }
-            yv[2] = ld<T, C>(d_xy, o) * v[2] + ld<T, C>(a_xy, o) * ((zu - zu_rm) + (zv - zv_cm));
-            yv[3] = ld<T, C>(d_xz, o) * v[3] + ld<T, C>(a_xz, o) * ((zu - zu_qm) + (zw - zw_cm));
-            yv[4] = ld<T, C>(d_yz, o) * v[4] + ld<T, C>(a_yz, o) * ((zv - zv_qm) + (zw - zw_rm));
+            yv[2] = dxy * v[2] + axy * ((zu - zu_rm) + (zv - zv_cm));
+            yv[3] = dxz * v[3] + axz * ((zu - zu_qm) + (zw - zw_cm));
+            yv[4] = dyz * v[4] + ayz * ((zv - zv_qm) + (zw - zw_rm));
             if (MODE == MODE_RESID) {
                 const T* b = (const T*)args.b;
 #pragma unroll
@@ -858,6 +882,7 @@ static cudaError_t launch_mode(const Layout& L, const int* tiles, int ntiles, co
         // units (an apply over the active tiles needs the unit list) or all
         (void)cache3;
         if (tiles && !a.units) return cudaErrorInvalidValue;
+        if (sizeof(C) == 2 && !cf.qd[0]) return cudaErrorInvalidValue;   // BF16 reads the arrays in fours
         const int nu = tiles ? a.nunits : L.ntx * units_y(L.nty) * units_z(L.ntz, ZT_MAX);
         if (nu > 0) k_apply3d<T, C, MODE><<<nu, 256, sizeof(Smem3<T>), s>>>(L, cf, x, y, a);
     }

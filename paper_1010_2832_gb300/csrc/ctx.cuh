@@ -23,6 +23,7 @@ struct DevArrays {
     float* coef32;
     __nv_bfloat16* coef16;
     uint32_t* pair16;     // 2D: coef16 in pairs (see Coef)
+    uint2* quad16;        // 3D: coef16 in fours (see Coef)
     double* minv64;
     float* minv32;
     uint8_t* tile_flag;
@@ -129,6 +130,8 @@ template <> inline Coef<__nv_bfloat16> Ctx::coef<__nv_bfloat16>() const {
     for (int f = 0; f < ncoef; ++f) c.f[f] = A.coef16 + (int64_t)f * L.stride;
     if (L.dim == 2 && A.pair16)
         for (int k = 0; k < 3; ++k) c.pr[k] = A.pair16 + (int64_t)k * L.stride;
+    if (L.dim == 3 && A.quad16)
+        for (int k = 0; k < 2; ++k) c.qd[k] = A.quad16 + (int64_t)k * L.stride;
     return c;
 }
 

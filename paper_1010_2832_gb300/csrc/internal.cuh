@@ -44,11 +44,14 @@ enum : uint8_t { F_LIVE = 1, F_BAD = 2, F_INVALID = 4, F_WALL = 8, F_EXISTS = 16
 // stress unknowns, 1 on inactive ones; K = dt W_F / (rho W_L) on live faces.
 // 2D BF16 coefficients are also stored in pairs, one 32-bit word per slot
 // (first coefficient in the low half): (a_c, a_n), (d_c, d_n), (K_u, K_v),
-// so that one 16-byte load brings two coefficients of four slots (nullptr
-// in other precisions and in 3D).
+// so that one 16-byte load brings two coefficients of four slots; 3D BF16
+// coefficients also in fours, 8 bytes per slot (first in the low half of
+// .x): (a_c, a_xy, a_xz, a_yz) and (d_c, d_xy, d_xz, d_yz), so that a slot's
+// row weights or diagonal are one load (nullptr where not stored).
 template <class C> struct Coef {
     const C* f[11];
     const uint32_t* pr[3];
+    const uint2* qd[2];
 };
 
 // Device-resident scalars of one CG solve.

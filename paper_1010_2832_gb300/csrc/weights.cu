@@ -604,11 +604,17 @@ __global__ void k_finish3d(Layout L, DevArrays D) {
     D.coef64[8 * S + o] = Ku[o];
     D.coef64[9 * S + o] = Kv[o];
     D.coef64[10 * S + o] = Kw[o];
+    uint32_t h[8];
     for (int f = 0; f < 11; ++f) {
         double v = D.coef64[(int64_t)f * S + o];
         D.coef32[(int64_t)f * S + o] = (float)v;
-        D.coef16[(int64_t)f * S + o] = __double2bfloat16(v);
+        const __nv_bfloat16 b = __double2bfloat16(v);
+        D.coef16[(int64_t)f * S + o] = b;
+        if (f < 8) h[f] = __bfloat16_as_ushort(b);
     }
+    // the same BF16 values in fours: (a_c, a_xy, a_xz, a_yz), (d_c, d_xy, d_xz, d_yz)
+    for (int k = 0; k < 2; ++k)
+        D.quad16[(int64_t)k * S + o] = make_uint2(h[4 * k] | (h[4 * k + 1] << 16), h[4 * k + 2] | (h[4 * k + 3] << 16));
     for (int f = 0; f < 6; ++f) D.minv32[(int64_t)f * S + o] = (float)D.minv64[(int64_t)f * S + o];
     if (tile_act) {
         int c = i + 1, r = j + 1, q = k + 1;
