@@ -220,17 +220,18 @@ __global__ void __launch_bounds__(256, MINB) k_apply2d(Layout L, const int* __re
 // is four groups of 64, each working on its own 32 x 8 tile of the list
 // (persistent: group g of CTA b takes tiles 4 b + g, 4 b + g + 4 G, ...)
 // and synchronising on its own named barrier.  Every load of a row's 32
-// slots is one 16-byte load per field for the vectors (8 bytes for BF16
-// coefficients, 16 for FP32), plus scalar loads for the two halo columns:
-// about 5 load instructions per slot against 17 with one slot per thread.
+// slots is one 16-byte load per field for the vectors and FP32 coefficients,
+// and per pair of fields for BF16 coefficients (the pair arrays of Coef),
+// plus scalar loads for the two halo columns: about 5 load instructions per
+// slot against 17 with one slot per thread.
 // Every load of a tile is issued before any is used (one memory round trip
 // per tile; 127 registers, two CTAs = eight tiles in flight per SM): FP32 on
 // a 4096^2 box 0.77 of the measured HBM bandwidth (one slot per thread,
 // software-pipelined: 0.69; this layout with a round trip per phase: 0.63).
 // The arithmetic of each slot is that of apply2d_tile, in the same order.
-// Four consecutive coefficients as loaded (R: float4, or uint2 holding four
-// BF16 values, converted only where used, so that a tile's loads in flight
-// take half the registers) and as FP32.
+// Four consecutive coefficients of one field as loaded (R: float4) and as
+// FP32.  The kernel reads BF16 coefficients from the pair arrays instead;
+// V4<__nv_bfloat16> only types its field-by-field branch, unused for BF16.
 template <class C> struct V4;
 template <> struct V4<float> {
     using R = float4;
