@@ -131,6 +131,57 @@ def additive_schwarz(S, r, core=4, ring=1):
     return z
 
 
+def schwarz_colour_patches(S, core=4, ring=1):
+    """The patches of ``additive_schwarz`` (same cores, same widening), each
+    with its colour (I mod 2) + 2 (J mod 2): [(colour, indices), ...].  Cores
+    of one colour are one core apart, so with 2 ring <= core their widened
+    patches are pairwise disjoint."""
+    si, sj = slot_coordinates_2d(S)
+    act = S.active
+    nx, ny = S.inp.n
+    out = []
+    for J in range(0, (ny + 1 + core - 1) // core):
+        for I in range(0, (nx + 1 + core - 1) // core):
+            incore = act & (si >= core * I) & (si < core * I + core) & (sj >= core * J) & (sj < core * J + core)
+            if not incore.any():
+                continue
+            m = act & (si >= core * I - ring) & (si < core * I + core + ring) & \
+                (sj >= core * J - ring) & (sj < core * J + core + ring)
+            out.append(((I % 2) + 2 * (J % 2), np.flatnonzero(m)))
+    return out
+
+
+def multiplicative_schwarz(S, r, core=4, ring=1, order=(0, 1, 2, 3, 2, 1, 0)):
+    """Symmetric multiplicative overlapping Schwarz (2D), the form of
+    preconditioner the paper used with CG (Section 9, the paragraph before
+    Table solveriterations), on the patches of ``additive_schwarz`` coloured
+    by ``schwarz_colour_patches``.  Starting from z = 0 and the residual
+    e = r, each colour c of ``order`` in turn solves the local problems of
+    its patches on the current residual, adds the corrections to z and
+    updates the residual:
+
+        d = sum_{p in c} R_p^T (R_p A R_p^T)^-1 R_p e,   z += d,   e -= A d.
+
+    The patches of one colour are disjoint, so their solves are independent.
+    A palindromic order makes the operator symmetric; its error propagator
+    is I - M A = (I - B_c1 A)(I - B_c2 A) ... (I - B_c1 A) with
+    B_c = sum_{p in c} R_p^T A_p^-1 R_p.  Inactive unknowns: z = r.  Dense
+    FP64 local solves."""
+    A = S.A.tocsr()
+    act = S.active
+    patches = schwarz_colour_patches(S, core, ring)
+    z = np.zeros(r.size)
+    e = np.where(act, r, 0.0)
+    for c in order:
+        d = np.zeros(r.size)
+        for colour, idx in patches:
+            if colour == c:
+                d[idx] += np.linalg.solve(A[idx][:, idx].toarray(), e[idx])
+        z += d
+        e -= A @ d
+    return np.where(act, z, r)
+
+
 def time_pcg_iterations(A, b, iters):
     """Wall time of ``iters`` iterations of ``pcg`` (no convergence test), for
     the CPU baseline.  Returns seconds."""
