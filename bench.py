@@ -19,6 +19,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -32,24 +33,41 @@ sys.path.insert(0, ROOT)
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
-# Source files of each reported kernel (the ncu traffic below is valid only
-# for the hash of these files it was taken with; see profiles/).
+# Sources of each reported kernel: whole files, or (file, struct names) for
+# the definitions of the types a kernel takes from a shared header (the ncu
+# traffic below is valid only for the hash of these sources it was taken
+# with; see profiles/).
 KERNEL_SOURCES = {
-    "k_schwarz_gemv": ("schwarz.cuh", "schwarz_plan.cuh", "internal.cuh", "ctx.cuh"),
+    "k_schwarz_gemv": ("schwarz.cuh", "schwarz_plan.cuh", ("internal.cuh", ("Layout", "CgScalars"))),
     "k_apply2d": ("apply.cu", "apply2d_tile.cuh", "internal.cuh", "ctx.cuh"),
     "k_apply3d": ("apply.cu", "internal.cuh", "ctx.cuh"),
 }
 # (workload, mode, kernel) -> (source hash, dram__bytes_read.sum +
 # dram__bytes_write.sum per launch from one ncu capture of the same command)
 NCU_TRAFFIC = {
-    ("bumps1024", "fp32", "k_schwarz_gemv"): ("5b8e7f14a3700538", 244.706048e6),   # ncu capture of this command
+    ("bumps1024", "fp32", "k_schwarz_gemv"): ("fff896e2cd21474e", 244.706048e6),   # ncu capture of this command
 }
 
 
-def kernel_source_hash(kernel):
+def struct_source(text, name):
+    """The definition of ``struct name`` in a header: from its opening line to
+    the first ``};`` at the start of a line."""
+    m = re.search(r"^struct " + re.escape(name) + r" \{.*?^\};", text, re.S | re.M)
+    if m is None:
+        raise KeyError(f"struct {name} not found")
+    return m.group(0)
+
+
+def kernel_source_hash(kernel, csrc=None):
+    csrc = csrc or os.path.join(ROOT, "paper_1010_2832_gb300", "csrc")
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[kernel]:
-        h.update(open(os.path.join(ROOT, "paper_1010_2832_gb300", "csrc", f), "rb").read())
+        if isinstance(f, tuple):
+            text = open(os.path.join(csrc, f[0])).read()
+            for name in f[1]:
+                h.update(struct_source(text, name).encode())
+        else:
+            h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 

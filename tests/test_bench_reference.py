@@ -51,3 +51,29 @@ def test_window_face_index_map():
     flat_win = np.concatenate([f.ravel() for f in win_vals])
     idx = np.arange(flat_win.size)
     assert np.array_equal(flat_full[bench.window_face_to_full(idx, n, win)], flat_win)
+
+
+def test_kernel_source_hash_follows_the_kernel_and_its_argument_types(tmp_path):
+    """The stored ncu traffic of the local-solve kernel is reported only while
+    the hash of its sources matches: the hash changes with the kernel's files
+    and with the definitions of the types it takes (Layout, CgScalars), and
+    not with other declarations of the shared header."""
+    import shutil
+    import bench
+    src = os.path.join(ROOT, "paper_1010_2832_gb300", "csrc")
+    for f in ("schwarz.cuh", "schwarz_plan.cuh", "internal.cuh"):
+        shutil.copy(os.path.join(src, f), tmp_path / f)
+    h0 = bench.kernel_source_hash("k_schwarz_gemv", str(tmp_path))
+    assert h0 == bench.kernel_source_hash("k_schwarz_gemv")
+    internal = (tmp_path / "internal.cuh").read_text()
+    # another declaration of the header: same hash
+    (tmp_path / "internal.cuh").write_text(internal.replace("struct ApplyArgs {", "struct ApplyArgs {\n    int unused_;"))
+    assert bench.kernel_source_hash("k_schwarz_gemv", str(tmp_path)) == h0
+    # a field of Layout: new hash
+    (tmp_path / "internal.cuh").write_text(internal.replace("    int ntx, nty, ntz;", "    int ntx, nty, ntz, extra;"))
+    assert bench.kernel_source_hash("k_schwarz_gemv", str(tmp_path)) != h0
+    (tmp_path / "internal.cuh").write_text(internal)
+    # the kernel's own file: new hash
+    with open(tmp_path / "schwarz.cuh", "a") as f:
+        f.write("\n// edit\n")
+    assert bench.kernel_source_hash("k_schwarz_gemv", str(tmp_path)) != h0
